@@ -1,0 +1,179 @@
+/*
+ * hpr.h -- C ABI of the B300 HPR-LP solver (CUDA, sm_103a).
+ *
+ * Solves the linear program of Section 1, eq. (1) of Chen, Sun, Yuan, Zhang & Zhao,
+ * "HPR-LP: An implementation of an HPR method for solving linear programming"
+ * (arXiv 2408.12179):
+ *
+ *     min <c, x>   s.t.   A1 x = b1,   A2 x >= b2,   l <= x <= u,
+ *
+ * and its dual eq. (2), with the Halpern Peaceman-Rachford method of Algorithm 2
+ * (semi-proximal term T1 = lambda I - A A^*, Section 3.3), the restart criteria of
+ * Section 3.1, the sigma update of Algorithm 3 / eq. (sigma_T1!=0), and the
+ * preprocessing, power method and termination test of Section 4.1.
+ *
+ * Conventions for every entry point:
+ *   - all array arguments are HOST pointers unless stated otherwise;
+ *   - nothing is retained: hpr_create deep-copies its inputs to the GPU, the caller
+ *     may free them on return; every device allocation belongs to the context and is
+ *     released by hpr_destroy;
+ *   - errors are returned as a status code (never thrown across the ABI); the detail
+ *     of the last error of a context is in hpr_last_error();
+ *   - a context is not thread-safe; separate contexts are independent.  A context
+ *     uses the CUDA device that was current when it was created.
+ */
+#ifndef HPR_H
+#define HPR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+enum {
+    HPR_OK = 0,              /* converged: KKT residual <= tol (Section 4.1) */
+    HPR_MAX_ITER = 1,        /* iteration limit reached; the last w_bar is retrievable */
+    HPR_TIME_LIMIT = 2,      /* time limit reached; the last w_bar is retrievable */
+    HPR_ERR_ARG = -1,        /* NULL / inconsistent sizes, unsorted or duplicate column
+                                indices, non-finite data, l > u, l = +inf or u = -inf */
+    HPR_ERR_ZERO_MATRIX = -2,/* A has no nonzero entry (Section 1 assumes A != 0) */
+    HPR_ERR_NOMEM = -3,      /* device or pinned host allocation failed */
+    HPR_ERR_CUDA = -4,       /* any other CUDA runtime error */
+    HPR_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait gave up */
+    HPR_ERR_NUMERIC = -6,    /* a residual became NaN or infinite */
+    HPR_ERR_STATE = -7,      /* call out of order (e.g. results requested before a solve) */
+    HPR_ERR_NO_DEVICE = -8   /* no CUDA device or not an sm_103 device */
+};
+
+typedef struct hpr_ctx hpr_ctx;
+
+/* A sparse block in CSR form (host arrays).  row_ptr[0] = 0, row_ptr[rows] = nnz,
+ * non-decreasing; col_idx strictly increasing within a row and in [0, cols); val
+ * finite.  A block with rows = 0 may pass NULL arrays; a NULL hpr_csr* means an
+ * empty block. */
+typedef struct {
+    int64_t rows, cols, nnz;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const double *val;
+} hpr_csr;
+
+/* Solver options.  hpr_default_options() fills the paper's settings (Section 4.1). */
+typedef struct {
+    double tol;               /* stopping tolerance eps of Section 4.1 (1e-8) */
+    int64_t max_iter;         /* iteration limit (10,000,000) */
+    double time_limit_s;      /* wall-clock limit of hpr_solve; <= 0: none */
+    int64_t check_every;      /* termination / restart check period (150, Section 4.1) */
+    double alpha1, alpha2, alpha3; /* restart parameters (0.2, 0.6, 0.2, Section 4.1) */
+    double sigma0;            /* initial penalty parameter (1) */
+    int64_t ruiz_iters;       /* Ruiz iterations (10) */
+    double pc_alpha;          /* Pock-Chambolle alpha (1); negative disables that step */
+    int64_t power_max_iter;   /* power-method iteration cap (5000) */
+    double power_tol;         /* stop when |lambda_k - lambda_{k-1}| <= tol lambda_k (1e-10) */
+    uint64_t seed;            /* SplitMix64 seed of the power-method start vector */
+    double lambda_fixed;      /* > 0: use this lambda (T1 = lambda I - A A^*) and skip the
+                                 power method; 0: power method (default) */
+    int64_t restart;          /* 0 disables the restart criteria (ablation) */
+    int64_t sigma_update;     /* 0 keeps sigma at restarts (ablation) */
+    int64_t trace_iters;      /* record the scaled iterates of the first trace_iters
+                                 iterations (for parity checks; slow) */
+    int64_t use_graph;        /* 1: run each check period as one captured CUDA graph */
+    int64_t verbose;          /* 1: print one line per check to stderr */
+    void *cuda_stream;        /* cudaStream_t to order the work after; NULL: the
+                                 context's own stream */
+} hpr_options;
+
+/* Result summary (original, unscaled problem). */
+typedef struct {
+    double primal_obj, dual_obj;  /* <c,x> and <b,y> - delta_C^*(-z) */
+    double err_p, err_d, err_gap; /* relative residuals of Section 4.1 */
+    double kkt;                   /* max(err_p, err_d, err_gap) */
+    double sigma, lambda;         /* final penalty parameter; lambda of T1 */
+    double solve_time_s;          /* power method + iterations (Section 4.1 timing) */
+    double power_time_s;          /* power method alone */
+    double time_to_1e4_s;         /* first check with kkt <= 1e-4 (-1 if none) */
+    int64_t iters_to_1e4;         /* iterations at that check (-1 if none) */
+    int64_t iters, restarts, power_iters, n_checks;
+    int64_t launches;             /* kernels launched by the solve (graph nodes included) */
+    int64_t status;               /* HPR_OK, HPR_MAX_ITER or HPR_TIME_LIMIT */
+} hpr_info;
+
+/* One evaluation of the restart / termination quantities.  kind: 1 = periodic check,
+ * 2 = R~_{r,0} at the first iteration of an inner loop, 3 = both.  cause: 0 none,
+ * 1..3 = restart criterion eq. (restart_1)..(restart_3), -1 = terminated. */
+typedef struct {
+    int64_t k, r, t, kind, cause;
+    double sigma, err_p, err_d, err_gap, kkt, pobj, dobj;
+    double Rt, R0, sigma_next, Dx, Dy, elapsed_s;
+} hpr_check_record;
+
+/* Fills *opt with the defaults above.  Returns HPR_OK or HPR_ERR_ARG (opt NULL). */
+int hpr_default_options(hpr_options *opt);
+
+/* Validates and uploads the LP of eq. (1), builds the explicit CSR of A^T, and runs the
+ * preprocessing of Section 4.1 on the GPU (Ruiz, Pock-Chambolle, b/c normalisation).
+ * A1 is m1 x n, A2 is m2 x n (either may be NULL or have rows = 0, not both empty);
+ * b1 (m1), b2 (m2), c, l, u (n) are host arrays; l may hold -inf, u +inf.
+ * opt may be NULL (defaults).  On success *out owns all device memory. */
+int hpr_create(hpr_ctx **out, const hpr_csr *A1, const hpr_csr *A2, const double *b1,
+               const double *b2, const double *c, const double *l, const double *u,
+               const hpr_options *opt);
+
+/* Replaces the context's options (the preprocessing already done is kept; ruiz_iters
+ * and pc_alpha take effect only at creation). */
+int hpr_set_options(hpr_ctx *ctx, const hpr_options *opt);
+
+/* Runs the power method of Section 4.1 on the scaled A: lambda_1(A A^*).  Writes
+ * lambda and the number of iterations (either pointer may be NULL). */
+int hpr_power(hpr_ctx *ctx, double *lambda, int64_t *iters);
+
+/* Runs Algorithm 2 from the origin with sigma_0 (Section 4.1) until the termination
+ * test holds for tol (> 0; overrides opt.tol), max_iter or time_limit_s.  Returns
+ * HPR_OK, HPR_MAX_ITER, HPR_TIME_LIMIT or an error. */
+int hpr_solve(hpr_ctx *ctx, double tol);
+
+/* Copies the last w_bar of hpr_solve, mapped back to the original LP (x projected
+ * onto C), into caller-allocated host arrays x (n), y (m1+m2), z (n) and the summary
+ * into *info; any pointer may be NULL.  HPR_ERR_STATE before the first solve. */
+int hpr_get(const hpr_ctx *ctx, double *x, double *y, double *z, hpr_info *info);
+
+/* Preprocessing results: D_r (m), D_c (n), the scaled values of A in the CSR order of
+ * [A1; A2] (nnz), the scaled b (m), c, l, u (n) and beta = {||D_r b||+1, ||D_c c||+1}
+ * (2).  Any pointer may be NULL. */
+int hpr_get_scaling(const hpr_ctx *ctx, double *Dr, double *Dc, double *As_val,
+                    double *bs, double *cs, double *ls, double *us, double *beta);
+
+/* The check records of the last solve, in order: copies min(cap, count) records into
+ * out (may be NULL with cap 0) and the count into *count. */
+int hpr_get_checks(const hpr_ctx *ctx, hpr_check_record *out, int64_t cap, int64_t *count);
+
+/* Scaled-space iterates of iteration k (0-based, k < trace_iters and < iterations
+ * run) of the last solve: x_bar, x_hat (n), x after the Halpern / restart step (n),
+ * y_bar (m) and y after the step (m).  Any pointer may be NULL. */
+int hpr_get_trace(const hpr_ctx *ctx, int64_t k, double *xbar, double *xhat, double *x,
+                  double *ybar, double *y);
+
+/* Times `reps` plain HPR iterations (Section 3.3: the A^T phase with the x update,
+ * then the A phase with the y update) launched one kernel at a time, with CUDA events
+ * around each kernel on the context's stream.  Starts from the current iterate and
+ * advances it (call after hpr_solve).  Writes the average duration in milliseconds of
+ * the x phase (ms_x), the y phase (ms_y) and of a whole iteration (ms_iter); any
+ * pointer may be NULL.  HPR_ERR_STATE before the first solve. */
+int hpr_time_iteration(hpr_ctx *ctx, int64_t reps, double *ms_x, double *ms_y, double *ms_iter);
+
+/* Detail of the last error of ctx (a static string when ctx is NULL). */
+const char *hpr_last_error(const hpr_ctx *ctx);
+
+/* Name of a status code. */
+const char *hpr_status_str(int status);
+
+/* Frees everything the context owns.  NULL is ignored. */
+void hpr_destroy(hpr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPR_H */

@@ -1,0 +1,36 @@
+"""Build step of the solver's shared library (nvcc, sm_103a only).
+
+``python -m paper_2408_12179_b300.build`` compiles ``csrc/hpr_api.cu`` (which includes
+the device code in ``csrc/hpr_device.cuh``) into ``libhpr_b300.so`` beside this file:
+one C-ABI shared object with no torch dependency, the CUDA runtime linked statically.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = [os.path.join(HERE, "csrc", "hpr_api.cu")]
+DEPS = SRC + [os.path.join(HERE, "csrc", "hpr_device.cuh"), os.path.join(ROOT, "include", "hpr.h")]
+LIB = os.path.join(HERE, "libhpr_b300.so")
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc_cmd(out=LIB, extra=()):
+    return [NVCC, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
+            "-shared", "-I", os.path.join(ROOT, "include"), "-o", out, *SRC, *extra]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and os.path.exists(LIB):
+        newest = max(os.path.getmtime(p) for p in DEPS)
+        if os.path.getmtime(LIB) >= newest:
+            return LIB
+    extra = ["-Xptxas", "-v"] if verbose else []
+    subprocess.run(nvcc_cmd(extra=extra), check=True)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose="-v" in sys.argv))

@@ -1,0 +1,1139 @@
+// C ABI and host runtime of the B300 HPR-LP solver; declarations in include/hpr.h.
+//
+// Host responsibilities: validate the LP, assemble A = [A1; A2], build the explicit
+// CSR of A^T (stable counting sort) and the tile schedules of both matrices, drive
+// the preprocessing / power-method / iteration kernels, and take the scalar decisions
+// of Algorithm 2 (termination, restart criteria of Section 3.1, Algorithm 3) once per
+// check period from ~16 reduced FP64 scalars.  Every vector operation of the method
+// runs in the kernels of hpr_device.cuh.
+//
+// Iteration schedule (same reading as the documentation of the method's oracle):
+// iteration k (0-based) maps w^k to w^{k+1}; it is a check when (k+1) % check_every == 0
+// or k+1 == max_iter, and evaluates R~_{r,0} when the inner counter t is 0.  Restarts
+// happen only at checks, so every check period is one batch of iterations whose last
+// iteration is a check and whose first is an R~_{r,0} evaluation right after a restart:
+// the batch is captured once as a CUDA graph and replayed.
+#include "hpr.h"
+#include "hpr_device.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace hprdev;
+
+namespace {
+
+struct GraphKey {
+    int L;
+    int first;
+    bool operator<(const GraphKey &o) const { return L != o.L ? L < o.L : first < o.first; }
+};
+
+}  // namespace
+
+struct hpr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    hpr_options opt{};
+    int64_t m1 = 0, m2 = 0, m = 0, n = 0, nnz = 0;
+    double norm_b = 0.0, norm_c = 0.0, beta_b = 1.0, beta_c = 1.0;
+
+    // matrices (device): scaled A, its explicit transpose and the transpose map
+    int *A_rp = nullptr, *A_ci = nullptr;
+    double *A_val = nullptr;
+    int *T_rp = nullptr, *T_ci = nullptr, *T_perm = nullptr;
+    double *T_val = nullptr;
+    int *tilesA = nullptr, *tilesT = nullptr;
+    int ntA = 0, ntT = 0;
+
+    // vectors (device)
+    double *Dr = nullptr, *Dc = nullptr, *wr = nullptr, *wc = nullptr;
+    double *b_s = nullptr, *c_s = nullptr, *l_s = nullptr, *u_s = nullptr;
+    double *l_o = nullptr, *u_o = nullptr;
+    double *x = nullptr, *x0 = nullptr, *xhat = nullptr, *xbar = nullptr, *zbar = nullptr,
+           *dx = nullptr;
+    double *y = nullptr, *y0 = nullptr, *ybar = nullptr, *dy = nullptr;
+    double *xo = nullptr, *yo = nullptr, *zo = nullptr;
+
+    // reductions and control
+    double *partials = nullptr;
+    int pstride = 0;
+    double *scal = nullptr;     // device, 2 slots of NQ
+    double *scal_h = nullptr;   // pinned mirror
+    DevCtl *ctl = nullptr;      // device control block
+    DevCtl *ctl_h = nullptr;    // pinned staging
+    size_t ctl_bytes = 0;
+    int ctl_cap = 0;
+    PowCtl *pctl = nullptr, *pctl_h = nullptr;
+    double *trace = nullptr;
+    int64_t trace_n = 0;
+    int64_t trace_written = 0;
+
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<GraphKey, int64_t> graph_launches;   // kernel nodes per captured period
+    cudaGraphExec_t pow_graph = nullptr;
+    int64_t launches = 0;                           // kernels launched by the current solve
+
+    // results
+    bool solved = false;
+    bool have_power = false;
+    double lambda = 0.0;
+    int64_t power_iters = 0;
+    double power_time = 0.0;
+    hpr_info info{};
+    std::vector<hpr_check_record> checks;
+    std::string err;
+};
+
+namespace {
+
+const char *g_static_err = "no context";
+
+int fail_cuda(hpr_ctx *c, cudaError_t e, const char *what, int line)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s failed at line %d: %s (%s)", what, line, cudaGetErrorName(e),
+             cudaGetErrorString(e));
+    if (c) c->err = buf;
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? HPR_ERR_NOMEM : HPR_ERR_CUDA;
+}
+
+int fail_arg(hpr_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) return fail_cuda(ctx, e_, #call, __LINE__);        \
+    } while (0)
+
+#define CKL()                                                                     \
+    do {                                                                          \
+        cudaError_t e_ = cudaGetLastError();                                      \
+        if (e_ != cudaSuccess) return fail_cuda(ctx, e_, "kernel launch", __LINE__); \
+    } while (0)
+
+template <class T>
+int dalloc(hpr_ctx *ctx, T **p, int64_t count)
+{
+    size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail_cuda(ctx, e, "cudaMalloc", __LINE__);
+    }
+    return HPR_OK;
+}
+
+#define DALLOC(p, cnt)                          \
+    do {                                        \
+        int s_ = dalloc(ctx, &(p), (cnt));      \
+        if (s_ != HPR_OK) return s_;            \
+    } while (0)
+
+int grid_for(int64_t n, int threads = 256, int cap = 148 * 16)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// Tile schedule: consecutive rows, at most TILE_ROWS rows and TILE_NNZ nonzeros per
+// tile; a row longer than TILE_NNZ is a tile of its own.
+std::vector<int> build_tiles(const std::vector<int> &rp, int rows)
+{
+    std::vector<int> t;
+    t.push_back(0);
+    int r = 0;
+    while (r < rows) {
+        const int start = r;
+        if (rp[r + 1] - rp[r] > TILE_NNZ) {
+            ++r;
+        } else {
+            while (r < rows && r - start < TILE_ROWS && rp[r + 1] - rp[start] <= TILE_NNZ) ++r;
+        }
+        t.push_back(r);
+    }
+    return t;
+}
+
+int validate_block(hpr_ctx *ctx, const hpr_csr *B, const char *name, int64_t *rows, int64_t *cols)
+{
+    if (!B || B->rows == 0) {
+        *rows = 0;
+        *cols = B ? B->cols : -1;
+        if (B && B->nnz != 0) return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": rows = 0 but nnz != 0");
+        return HPR_OK;
+    }
+    if (B->rows < 0 || B->cols < 0 || B->nnz < 0)
+        return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": negative size");
+    if (!B->row_ptr || (B->nnz > 0 && (!B->col_idx || !B->val)))
+        return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": NULL array");
+    if (B->row_ptr[0] != 0 || B->row_ptr[B->rows] != B->nnz)
+        return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": row_ptr[0] != 0 or row_ptr[rows] != nnz");
+    for (int64_t i = 0; i < B->rows; ++i) {
+        const int64_t a = B->row_ptr[i], b = B->row_ptr[i + 1];
+        if (b < a) return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": row_ptr decreases");
+        for (int64_t p = a; p < b; ++p) {
+            const int32_t cidx = B->col_idx[p];
+            if (cidx < 0 || cidx >= B->cols)
+                return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": column index out of range");
+            if (p > a && cidx <= B->col_idx[p - 1])
+                return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": column indices not strictly increasing in a row");
+            if (!std::isfinite(B->val[p]))
+                return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": non-finite value");
+        }
+    }
+    *rows = B->rows;
+    *cols = B->cols;
+    return HPR_OK;
+}
+
+void free_all(hpr_ctx *c)
+{
+    if (!c) return;
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    if (c->pow_graph) cudaGraphExecDestroy(c->pow_graph);
+    c->pow_graph = nullptr;
+    void *dev[] = {c->A_rp, c->A_ci, c->A_val, c->T_rp, c->T_ci, c->T_perm, c->T_val,
+                   c->tilesA, c->tilesT, c->Dr, c->Dc, c->wr, c->wc, c->b_s, c->c_s,
+                   c->l_s, c->u_s, c->l_o, c->u_o, c->x, c->x0, c->xhat, c->xbar,
+                   c->zbar, c->dx, c->y, c->y0, c->ybar, c->dy, c->xo, c->yo, c->zo,
+                   c->partials, c->scal, c->ctl, c->pctl, c->trace};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (c->scal_h) cudaFreeHost(c->scal_h);
+    if (c->ctl_h) cudaFreeHost(c->ctl_h);
+    if (c->pctl_h) cudaFreeHost(c->pctl_h);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------- launches
+
+int launch_reduce(hpr_ctx *ctx, const std::vector<std::pair<int, int>> &qc, double *out,
+                  const int *skip = nullptr)
+{
+    RedSpec s{};
+    s.nq = 0;
+    for (auto &p : qc) {
+        if (p.second <= 0) continue;
+        s.q[s.nq] = p.first;
+        s.cnt[s.nq] = p.second;
+        s.nq++;
+    }
+    // quantities without any partial (empty side) are zero
+    for (auto &p : qc)
+        if (p.second <= 0) CK(cudaMemsetAsync(out + p.first, 0, sizeof(double), ctx->stream));
+    if (s.nq == 0) return HPR_OK;
+    k_reduce<<<s.nq, TB, 0, ctx->stream>>>(ctx->partials, ctx->pstride, s, out, skip);
+    CKL();
+    ctx->launches += 1;
+    return HPR_OK;
+}
+
+XArgs xargs(hpr_ctx *c)
+{
+    XArgs a;
+    a.tiles = c->tilesT; a.rp = c->T_rp; a.ci = c->T_ci; a.val = c->T_val; a.y = c->y;
+    a.c = c->c_s; a.l = c->l_s; a.u = c->u_s; a.x0 = c->x0; a.x = c->x; a.xhat = c->xhat;
+    a.xbar = c->xbar; a.zbar = c->zbar; a.dx = c->dx; a.partials = c->partials;
+    a.pstride = c->pstride; a.ctl = c->ctl;
+    return a;
+}
+
+YArgs yargs(hpr_ctx *c)
+{
+    YArgs a;
+    a.tiles = c->tilesA; a.rp = c->A_rp; a.ci = c->A_ci; a.val = c->A_val; a.xhat = c->xhat;
+    a.b = c->b_s; a.y0 = c->y0; a.y = c->y; a.ybar = c->ybar; a.dy = c->dy;
+    a.partials = c->partials; a.pstride = c->pstride; a.m1 = (int)c->m1; a.ctl = c->ctl;
+    return a;
+}
+
+// one HPR iteration (phase X then phase Y); a check iteration also runs the two
+// residual passes and reduces everything into scal slot `slot`
+int enqueue_iteration(hpr_ctx *ctx, int it, bool check, int slot)
+{
+    ctx->launches += (ctx->ntT ? 1 : 0) + (ctx->ntA ? 1 : 0);
+    if (check) {
+        ctx->launches += (ctx->ntT ? 1 : 0) + (ctx->ntA ? 1 : 0);
+        if (ctx->ntT) k_phase_x<true><<<ctx->ntT, TB, 0, ctx->stream>>>(xargs(ctx), it);
+        CKL();
+        if (ctx->ntA) k_phase_y<true><<<ctx->ntA, TB, 0, ctx->stream>>>(yargs(ctx), it);
+        CKL();
+        DualArgs d;
+        d.tiles = ctx->tilesT; d.rp = ctx->T_rp; d.ci = ctx->T_ci; d.val = ctx->T_val;
+        d.ybar = ctx->ybar; d.c = ctx->c_s; d.zbar = ctx->zbar; d.wc = ctx->wc;
+        d.partials = ctx->partials; d.pstride = ctx->pstride;
+        if (ctx->ntT) k_check_dual<<<ctx->ntT, TB, 0, ctx->stream>>>(d);
+        CKL();
+        PrimalArgs p;
+        p.tiles = ctx->tilesA; p.rp = ctx->A_rp; p.ci = ctx->A_ci; p.val = ctx->A_val;
+        p.xbar = ctx->xbar; p.dx = ctx->dx; p.b = ctx->b_s; p.wr = ctx->wr; p.dy = ctx->dy;
+        p.partials = ctx->partials; p.pstride = ctx->pstride; p.m1 = (int)ctx->m1;
+        if (ctx->ntA) k_check_primal<<<ctx->ntA, TB, 0, ctx->stream>>>(p);
+        CKL();
+        const int nT = ctx->ntT, nA = ctx->ntA;
+        return launch_reduce(ctx, {{Q_DX2, nT}, {Q_XX0, nT}, {Q_CX, nT}, {Q_BND, nT},
+                                   {Q_DY2, nA}, {Q_YY0, nA}, {Q_BY, nA}, {Q_RD, nT},
+                                   {Q_RP, nA}, {Q_CROSS, nA}},
+                             ctx->scal + slot * NQ);
+    }
+    if (ctx->ntT) k_phase_x<false><<<ctx->ntT, TB, 0, ctx->stream>>>(xargs(ctx), it);
+    CKL();
+    if (ctx->ntA) k_phase_y<false><<<ctx->ntA, TB, 0, ctx->stream>>>(yargs(ctx), it);
+    CKL();
+    return HPR_OK;
+}
+
+int enqueue_period(hpr_ctx *ctx, int L, bool first_r0)
+{
+    for (int i = 0; i < L; ++i) {
+        const bool last = (i == L - 1);
+        const bool r0 = (i == 0 && first_r0);
+        int s = enqueue_iteration(ctx, i, last || r0, last ? 1 : 0);
+        if (s != HPR_OK) return s;
+    }
+    return HPR_OK;
+}
+
+int trace_copy(hpr_ctx *ctx, int64_t k)
+{
+    if (k >= ctx->trace_n) return HPR_OK;
+    const int64_t n = ctx->n, m = ctx->m;
+    double *rec = ctx->trace + (size_t)k * (size_t)(3 * n + 2 * m);
+    CK(cudaMemcpyAsync(rec, ctx->xbar, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(rec + n, ctx->xhat, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(rec + 2 * n, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(rec + 3 * n, ctx->ybar, sizeof(double) * m, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(rec + 3 * n + m, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->trace_written = std::max(ctx->trace_written, k + 1);
+    return HPR_OK;
+}
+
+int ensure_ctl(hpr_ctx *ctx, int cap)
+{
+    if (cap <= ctx->ctl_cap) return HPR_OK;
+    if (ctx->ctl) cudaFree(ctx->ctl);
+    if (ctx->ctl_h) cudaFreeHost(ctx->ctl_h);
+    ctx->ctl = nullptr;
+    ctx->ctl_h = nullptr;
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+    ctx->ctl_bytes = sizeof(DevCtl) + sizeof(double) * 2 * (size_t)cap;
+    CK(cudaMalloc((void **)&ctx->ctl, ctx->ctl_bytes));
+    CK(cudaMallocHost((void **)&ctx->ctl_h, ctx->ctl_bytes));
+    memset(ctx->ctl_h, 0, ctx->ctl_bytes);
+    ctx->ctl_cap = cap;
+    return HPR_OK;
+}
+
+// ---------------------------------------------------------------- power method
+
+int run_power(hpr_ctx *ctx)
+{
+    const int64_t m = ctx->m;
+    const int gm = (int)((m + TB - 1) / TB);
+    // u (m) in dy, s = A^T u (n) in dx, w = A s (m) in ybar
+    double *u = ctx->dy, *s = ctx->dx, *w = ctx->ybar;
+    k_pow_start<<<gm, TB, 0, ctx->stream>>>((int)m, ctx->opt.seed, u, ctx->partials, ctx->pstride);
+    CKL();
+    int st = launch_reduce(ctx, {{Q_V2, gm}}, ctx->scal);
+    if (st) return st;
+    double *invp = ctx->scal + Q_V2B;
+    k_inv_sqrt_scalar<<<1, 1, 0, ctx->stream>>>(ctx->scal, Q_V2, invp);
+    CKL();
+    k_scale_vec<<<grid_for(m), 256, 0, ctx->stream>>>((int)m, u, u, nullptr, invp);
+    CKL();
+
+    PowCtl pc{};
+    pc.tol = ctx->opt.power_tol;
+    pc.max_iter = (int)std::max<int64_t>(1, ctx->opt.power_max_iter);
+    *ctx->pctl_h = pc;
+    CK(cudaMemcpyAsync(ctx->pctl, ctx->pctl_h, sizeof(PowCtl), cudaMemcpyHostToDevice, ctx->stream));
+
+    auto enqueue_steps = [&](int steps) -> int {
+        for (int k = 0; k < steps; ++k) {
+            SpmvNormArgs a;
+            a.tiles = ctx->tilesT; a.rp = ctx->T_rp; a.ci = ctx->T_ci; a.val = ctx->T_val;
+            a.xin = u; a.out = s; a.partials = ctx->partials; a.pstride = ctx->pstride;
+            a.q = Q_S2; a.pc = ctx->pctl;
+            if (ctx->ntT) k_spmv_norm<<<ctx->ntT, TB, 0, ctx->stream>>>(a);
+            CKL();
+            int r = launch_reduce(ctx, {{Q_S2, ctx->ntT}}, ctx->scal, &ctx->pctl->done);
+            if (r) return r;
+            k_pow_after_s<<<1, 1, 0, ctx->stream>>>(ctx->pctl, ctx->scal);
+            CKL();
+            SpmvNormArgs b = a;
+            b.tiles = ctx->tilesA; b.rp = ctx->A_rp; b.ci = ctx->A_ci; b.val = ctx->A_val;
+            b.xin = s; b.out = w; b.q = Q_W2;
+            if (ctx->ntA) k_spmv_norm<<<ctx->ntA, TB, 0, ctx->stream>>>(b);
+            CKL();
+            r = launch_reduce(ctx, {{Q_W2, ctx->ntA}}, ctx->scal, &ctx->pctl->done);
+            if (r) return r;
+            k_pow_after_w<<<1, 1, 0, ctx->stream>>>(ctx->pctl, ctx->scal);
+            CKL();
+            k_scale_vec<<<grid_for(m), 256, 0, ctx->stream>>>((int)m, w, u, ctx->pctl, nullptr);
+            CKL();
+            k_pow_finish<<<1, 1, 0, ctx->stream>>>(ctx->pctl);
+            CKL();
+        }
+        return HPR_OK;
+    };
+
+    const int BATCH = 16;
+    if (ctx->opt.use_graph && !ctx->pow_graph) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t before = ctx->launches;
+        int r = enqueue_steps(BATCH);
+        ctx->launches = before;
+        cudaGraph_t gg = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &gg);
+        if (r) { if (gg) cudaGraphDestroy(gg); return r; }
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaStreamEndCapture", __LINE__);
+        g = gg;
+        e = cudaGraphInstantiate(&ctx->pow_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaGraphInstantiate", __LINE__);
+    }
+    ctx->launches += 3;   // start vector, 1/norm, normalisation (+1 for the reduction above)
+    for (int64_t done_steps = 0; done_steps <= ctx->opt.power_max_iter; done_steps += BATCH) {
+        if (ctx->opt.use_graph) {
+            ctx->launches += (int64_t)BATCH * 8;
+            CK(cudaGraphLaunch(ctx->pow_graph, ctx->stream));
+        } else {
+            ctx->launches += (int64_t)BATCH * 6;   // the 2 reductions count themselves
+            int r = enqueue_steps(BATCH);
+            if (r) return r;
+        }
+        CK(cudaMemcpyAsync(ctx->pctl_h, ctx->pctl, sizeof(PowCtl), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->pctl_h->done) break;
+    }
+    ctx->lambda = ctx->pctl_h->lam;
+    ctx->power_iters = ctx->pctl_h->k;
+    if (!std::isfinite(ctx->lambda) || !(ctx->lambda > 0.0))
+        return fail_arg(ctx, HPR_ERR_NUMERIC, "power method returned a non-positive lambda");
+    return HPR_OK;
+}
+
+// ---------------------------------------------------------------- create helpers
+
+int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const double *b1,
+                       const double *b2, const double *c, const double *l, const double *u)
+{
+    const int64_t m1 = ctx->m1, m2 = ctx->m2, m = ctx->m, n = ctx->n, nnz = ctx->nnz;
+
+    // assemble A = [A1; A2] with 32-bit offsets
+    std::vector<int> rp((size_t)m + 1);
+    std::vector<int> ci((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<double> val((size_t)std::max<int64_t>(nnz, 1));
+    int64_t off = 0;
+    rp[0] = 0;
+    const hpr_csr *blk[2] = {A1, A2};
+    const int64_t brows[2] = {m1, m2};
+    int64_t row = 0;
+    for (int bI = 0; bI < 2; ++bI) {
+        const hpr_csr *B = blk[bI];
+        for (int64_t i = 0; i < brows[bI]; ++i, ++row) {
+            for (int64_t p = B->row_ptr[i]; p < B->row_ptr[i + 1]; ++p, ++off) {
+                ci[(size_t)off] = B->col_idx[p];
+                val[(size_t)off] = B->val[p];
+            }
+            rp[(size_t)row + 1] = (int)off;
+        }
+    }
+    // explicit CSR of A^T by a stable counting sort (rows of A^T list the rows of A in
+    // increasing order) and the map from A^T positions to A positions
+    std::vector<int> trp((size_t)n + 1, 0), tci((size_t)std::max<int64_t>(nnz, 1)),
+        tperm((size_t)std::max<int64_t>(nnz, 1));
+    for (int64_t p = 0; p < nnz; ++p) trp[(size_t)ci[(size_t)p] + 1]++;
+    for (int64_t j = 0; j < n; ++j) trp[(size_t)j + 1] += trp[(size_t)j];
+    {
+        std::vector<int> next(trp.begin(), trp.end() - 1);
+        for (int64_t i = 0; i < m; ++i)
+            for (int p = rp[(size_t)i]; p < rp[(size_t)i + 1]; ++p) {
+                const int q = next[(size_t)ci[(size_t)p]]++;
+                tci[(size_t)q] = (int)i;
+                tperm[(size_t)q] = p;
+            }
+    }
+    std::vector<int> tA = build_tiles(rp, (int)m), tT = build_tiles(trp, (int)n);
+    ctx->ntA = (int)tA.size() - 1;
+    ctx->ntT = (int)tT.size() - 1;
+    ctx->pstride = std::max({ctx->ntA, ctx->ntT, (int)((std::max(m, n) + TB - 1) / TB), 1});
+
+    DALLOC(ctx->A_rp, m + 1); DALLOC(ctx->A_ci, nnz); DALLOC(ctx->A_val, nnz);
+    DALLOC(ctx->T_rp, n + 1); DALLOC(ctx->T_ci, nnz); DALLOC(ctx->T_perm, nnz); DALLOC(ctx->T_val, nnz);
+    DALLOC(ctx->tilesA, ctx->ntA + 1); DALLOC(ctx->tilesT, ctx->ntT + 1);
+    DALLOC(ctx->Dr, m); DALLOC(ctx->Dc, n); DALLOC(ctx->wr, m); DALLOC(ctx->wc, n);
+    DALLOC(ctx->b_s, m); DALLOC(ctx->c_s, n); DALLOC(ctx->l_s, n); DALLOC(ctx->u_s, n);
+    DALLOC(ctx->l_o, n); DALLOC(ctx->u_o, n);
+    DALLOC(ctx->x, n); DALLOC(ctx->x0, n); DALLOC(ctx->xhat, n); DALLOC(ctx->xbar, n);
+    DALLOC(ctx->zbar, n); DALLOC(ctx->dx, n);
+    DALLOC(ctx->y, m); DALLOC(ctx->y0, m); DALLOC(ctx->ybar, m); DALLOC(ctx->dy, m);
+    DALLOC(ctx->xo, n); DALLOC(ctx->yo, m); DALLOC(ctx->zo, n);
+    DALLOC(ctx->partials, (int64_t)NQ * ctx->pstride);
+    DALLOC(ctx->scal, 2 * NQ);
+    DALLOC(ctx->pctl, 1);
+    CK(cudaMallocHost((void **)&ctx->scal_h, sizeof(double) * 2 * NQ));
+    CK(cudaMallocHost((void **)&ctx->pctl_h, sizeof(PowCtl)));
+    int st = ensure_ctl(ctx, (int)std::min<int64_t>(ctx->opt.check_every, ctx->opt.max_iter));
+    if (st) return st;
+
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->A_rp, rp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->A_ci, ci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->A_val, val.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->T_rp, trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->T_ci, tci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->T_perm, tperm.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->tilesA, tA.data(), sizeof(int) * tA.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->tilesT, tT.data(), sizeof(int) * tT.size(), cudaMemcpyHostToDevice, s));
+    if (m1) CK(cudaMemcpyAsync(ctx->b_s, b1, sizeof(double) * m1, cudaMemcpyHostToDevice, s));
+    if (m2) CK(cudaMemcpyAsync(ctx->b_s + m1, b2, sizeof(double) * m2, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->c_s, c, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->l_s, l, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->u_s, u, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->l_o, l, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->u_o, u, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));   // host staging vectors go out of scope below
+
+    // ---- preprocessing of Section 4.1 (all on the GPU)
+    const int gm = grid_for(m), gn = grid_for(n), gz = grid_for(nnz);
+    k_fill<<<gm, 256, 0, s>>>(m, 1.0, ctx->Dr); CKL();
+    k_fill<<<gn, 256, 0, s>>>(n, 1.0, ctx->Dc); CKL();
+    double *dr = ctx->dy, *dc = ctx->dx;   // scratch
+    for (int64_t it = 0; it < ctx->opt.ruiz_iters; ++it) {
+        k_gather<<<gz, 256, 0, s>>>(nnz, ctx->A_val, ctx->T_perm, ctx->T_val); CKL();
+        k_row_absmax<<<gm, 256, 0, s>>>((int)m, ctx->A_rp, ctx->A_val, dr); CKL();
+        k_row_absmax<<<gn, 256, 0, s>>>((int)n, ctx->T_rp, ctx->T_val, dc); CKL();
+        k_factor<<<gm, 256, 0, s>>>((int)m, dr, ctx->Dr); CKL();
+        k_factor<<<gn, 256, 0, s>>>((int)n, dc, ctx->Dc); CKL();
+        k_scale_rows_cols<<<gm, 256, 0, s>>>((int)m, ctx->A_rp, ctx->A_ci, ctx->A_val, dr, dc); CKL();
+    }
+    if (ctx->opt.pc_alpha >= 0.0) {
+        const double al = ctx->opt.pc_alpha;
+        k_gather<<<gz, 256, 0, s>>>(nnz, ctx->A_val, ctx->T_perm, ctx->T_val); CKL();
+        k_row_abspow<<<gm, 256, 0, s>>>((int)m, ctx->A_rp, ctx->A_val, 2.0 - al, dr); CKL();
+        k_row_abspow<<<gn, 256, 0, s>>>((int)n, ctx->T_rp, ctx->T_val, al, dc); CKL();
+        k_factor<<<gm, 256, 0, s>>>((int)m, dr, ctx->Dr); CKL();
+        k_factor<<<gn, 256, 0, s>>>((int)n, dc, ctx->Dc); CKL();
+        k_scale_rows_cols<<<gm, 256, 0, s>>>((int)m, ctx->A_rp, ctx->A_ci, ctx->A_val, dr, dc); CKL();
+    }
+    k_gather<<<gz, 256, 0, s>>>(nnz, ctx->A_val, ctx->T_perm, ctx->T_val); CKL();
+
+    const int gv = (int)((std::max(m, n) + TB - 1) / TB);
+    k_prep_vectors<<<gv, TB, 0, s>>>((int)m, (int)n, ctx->Dr, ctx->Dc, ctx->b_s, ctx->c_s,
+                                      ctx->l_s, ctx->u_s, ctx->partials, ctx->pstride);
+    CKL();
+    st = launch_reduce(ctx, {{Q_V2, gv}, {Q_V2B, gv}}, ctx->scal);
+    if (st) return st;
+    CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double) * NQ, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->beta_b = std::sqrt(ctx->scal_h[Q_V2]) + 1.0;
+    ctx->beta_c = std::sqrt(ctx->scal_h[Q_V2B]) + 1.0;
+    k_prep_normalise<<<grid_for(std::max(m, n)), 256, 0, s>>>((int)m, (int)n, ctx->beta_b, ctx->beta_c,
+                                                              ctx->Dr, ctx->Dc, ctx->b_s, ctx->c_s,
+                                                              ctx->l_s, ctx->u_s, ctx->wr, ctx->wc);
+    CKL();
+    CK(cudaStreamSynchronize(s));
+    return HPR_OK;
+}
+
+double merit_from(const double *S, double sigma, double lambda)
+{
+    // ||w - w_hat||_M = 2 ||w - w_bar||_M, eq. (def:M) with T1 = lambda I - A A^*
+    const double q = sigma * lambda * S[Q_DY2] + 2.0 * S[Q_CROSS] + S[Q_DX2] / sigma;
+    return 2.0 * std::sqrt(q > 0.0 ? q : 0.0);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+int hpr_default_options(hpr_options *o)
+{
+    if (!o) return HPR_ERR_ARG;
+    memset(o, 0, sizeof *o);
+    o->tol = 1e-8;
+    o->max_iter = 10000000;
+    o->time_limit_s = 0.0;
+    o->check_every = 150;
+    o->alpha1 = 0.2;
+    o->alpha2 = 0.6;
+    o->alpha3 = 0.2;
+    o->sigma0 = 1.0;
+    o->ruiz_iters = 10;
+    o->pc_alpha = 1.0;
+    o->power_max_iter = 5000;
+    o->power_tol = 1e-10;
+    o->seed = 0x48505221ULL;
+    o->lambda_fixed = 0.0;
+    o->restart = 1;
+    o->sigma_update = 1;
+    o->trace_iters = 0;
+    o->use_graph = 1;
+    o->verbose = 0;
+    o->cuda_stream = nullptr;
+    return HPR_OK;
+}
+
+static int check_options(hpr_ctx *ctx, const hpr_options *o)
+{
+    if (!(o->tol > 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "tol must be > 0");
+    if (o->max_iter < 1) return fail_arg(ctx, HPR_ERR_ARG, "max_iter must be >= 1");
+    if (o->check_every < 1 || o->check_every > (1 << 20))
+        return fail_arg(ctx, HPR_ERR_ARG, "check_every must be in [1, 2^20]");
+    if (!(o->sigma0 > 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "sigma0 must be > 0");
+    if (o->ruiz_iters < 0) return fail_arg(ctx, HPR_ERR_ARG, "ruiz_iters must be >= 0");
+    if (o->power_max_iter < 1) return fail_arg(ctx, HPR_ERR_ARG, "power_max_iter must be >= 1");
+    if (o->trace_iters < 0) return fail_arg(ctx, HPR_ERR_ARG, "trace_iters must be >= 0");
+    if (!(o->lambda_fixed >= 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "lambda_fixed must be >= 0");
+    return HPR_OK;
+}
+
+int hpr_create(hpr_ctx **out, const hpr_csr *A1, const hpr_csr *A2, const double *b1,
+               const double *b2, const double *c, const double *l, const double *u,
+               const hpr_options *opt)
+{
+    if (!out) return HPR_ERR_ARG;
+    *out = nullptr;
+    hpr_ctx *ctx = new (std::nothrow) hpr_ctx();
+    if (!ctx) return HPR_ERR_NOMEM;
+    auto bail = [&](int code) {
+        g_static_err = "hpr_create failed (see hpr_last_error of a context)";
+        static thread_local std::string last;
+        last = ctx->err;
+        g_static_err = last.c_str();
+        free_all(ctx);
+        delete ctx;
+        return code;
+    };
+    if (opt) ctx->opt = *opt;
+    else hpr_default_options(&ctx->opt);
+    int st = check_options(ctx, &ctx->opt);
+    if (st) return bail(st);
+
+    int64_t r1 = 0, c1 = -1, r2 = 0, c2 = -1;
+    if ((st = validate_block(ctx, A1, "A1", &r1, &c1))) return bail(st);
+    if ((st = validate_block(ctx, A2, "A2", &r2, &c2))) return bail(st);
+    int64_t n = c1 >= 0 ? c1 : c2;
+    if (c1 >= 0 && c2 >= 0 && c1 != c2) return bail(fail_arg(ctx, HPR_ERR_ARG, "A1.cols != A2.cols"));
+    if (n <= 0) return bail(fail_arg(ctx, HPR_ERR_ARG, "n must be >= 1"));
+    const int64_t nnz = (r1 ? A1->nnz : 0) + (r2 ? A2->nnz : 0);
+    if (r1 + r2 == 0 || nnz == 0) return bail(fail_arg(ctx, HPR_ERR_ZERO_MATRIX, "A has no nonzero entry"));
+    if (nnz >= (int64_t)INT32_MAX || r1 + r2 >= (int64_t)INT32_MAX || n >= (int64_t)INT32_MAX)
+        return bail(fail_arg(ctx, HPR_ERR_ARG, "sizes beyond 2^31-1 are not supported"));
+    bool any_nonzero = false;
+    for (int bI = 0; bI < 2 && !any_nonzero; ++bI) {
+        const hpr_csr *B = bI ? A2 : A1;
+        const int64_t rows = bI ? r2 : r1;
+        if (!rows) continue;
+        for (int64_t p = 0; p < B->nnz; ++p)
+            if (B->val[p] != 0.0) { any_nonzero = true; break; }
+    }
+    if (!any_nonzero) return bail(fail_arg(ctx, HPR_ERR_ZERO_MATRIX, "A has no nonzero entry"));
+    if ((r1 && !b1) || (r2 && !b2) || !c || !l || !u)
+        return bail(fail_arg(ctx, HPR_ERR_ARG, "NULL vector"));
+    for (int64_t i = 0; i < r1; ++i)
+        if (!std::isfinite(b1[i])) return bail(fail_arg(ctx, HPR_ERR_ARG, "b1 not finite"));
+    for (int64_t i = 0; i < r2; ++i)
+        if (!std::isfinite(b2[i])) return bail(fail_arg(ctx, HPR_ERR_ARG, "b2 not finite"));
+    for (int64_t j = 0; j < n; ++j) {
+        if (!std::isfinite(c[j])) return bail(fail_arg(ctx, HPR_ERR_ARG, "c not finite"));
+        if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY || u[j] == -INFINITY)
+            return bail(fail_arg(ctx, HPR_ERR_ARG, "bounds must satisfy l <= u, l < +inf, u > -inf"));
+    }
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        ctx->err = "no CUDA device";
+        (void)cudaGetLastError();
+        return bail(HPR_ERR_NO_DEVICE);
+    }
+    cudaGetDevice(&ctx->device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess || prop.major != 10 ||
+        prop.minor != 3) {
+        (void)cudaGetLastError();
+        ctx->err = "this library is built for sm_103 (B300) only";
+        return bail(HPR_ERR_NO_DEVICE);
+    }
+    ctx->m1 = r1;
+    ctx->m2 = r2;
+    ctx->m = r1 + r2;
+    ctx->n = n;
+    ctx->nnz = nnz;
+    {
+        double sb = 0.0, sc = 0.0;
+        for (int64_t i = 0; i < r1; ++i) sb += b1[i] * b1[i];
+        for (int64_t i = 0; i < r2; ++i) sb += b2[i] * b2[i];
+        for (int64_t j = 0; j < n; ++j) sc += c[j] * c[j];
+        ctx->norm_b = std::sqrt(sb);
+        ctx->norm_c = std::sqrt(sc);
+    }
+    if (ctx->opt.cuda_stream) {
+        ctx->stream = (cudaStream_t)ctx->opt.cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(fail_cuda(ctx, e, "cudaStreamCreate", __LINE__));
+        ctx->own_stream = true;
+    }
+    st = upload_and_prepare(ctx, A1, A2, b1, b2, c, l, u);
+    if (st) return bail(st);
+    *out = ctx;
+    return HPR_OK;
+}
+
+int hpr_set_options(hpr_ctx *ctx, const hpr_options *opt)
+{
+    if (!ctx || !opt) return HPR_ERR_ARG;
+    int st = check_options(ctx, opt);
+    if (st) return st;
+    void *old_stream = ctx->opt.cuda_stream;
+    const int64_t ruiz = ctx->opt.ruiz_iters;
+    const double pca = ctx->opt.pc_alpha;
+    if (opt->seed != ctx->opt.seed || opt->power_tol != ctx->opt.power_tol ||
+        opt->power_max_iter != ctx->opt.power_max_iter)
+        ctx->have_power = false;
+    ctx->opt = *opt;
+    ctx->opt.cuda_stream = old_stream;   // the stream is fixed at creation
+    ctx->opt.ruiz_iters = ruiz;
+    ctx->opt.pc_alpha = pca;
+    return HPR_OK;
+}
+
+int hpr_power(hpr_ctx *ctx, double *lambda, int64_t *iters)
+{
+    if (!ctx) return HPR_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    int st = run_power(ctx);
+    if (st) return st;
+    ctx->have_power = true;
+    if (lambda) *lambda = ctx->lambda;
+    if (iters) *iters = ctx->power_iters;
+    return HPR_OK;
+}
+
+int hpr_solve(hpr_ctx *ctx, double tol)
+{
+    if (!ctx) return HPR_ERR_ARG;
+    if (!(tol > 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "tol must be > 0");
+    cudaSetDevice(ctx->device);
+    hpr_options &o = ctx->opt;
+    const int64_t n = ctx->n, m = ctx->m;
+    cudaStream_t s = ctx->stream;
+    ctx->solved = false;
+    ctx->checks.clear();
+    ctx->trace_written = 0;
+    int st;
+
+    // trace buffer
+    if (o.trace_iters > 0) {
+        const int64_t need = o.trace_iters;
+        if (need != ctx->trace_n) {
+            if (ctx->trace) cudaFree(ctx->trace);
+            ctx->trace = nullptr;
+            ctx->trace_n = 0;
+            DALLOC(ctx->trace, need * (3 * n + 2 * m));
+            ctx->trace_n = need;
+        }
+    }
+    st = ensure_ctl(ctx, (int)std::min<int64_t>(o.check_every, o.max_iter));
+    if (st) return st;
+
+    CK(cudaStreamSynchronize(s));
+    const double t0 = now_s();
+    ctx->launches = 0;
+
+    // ---- T1 = lambda I - A A^*: power method (counted in the solve time, Section 4.1)
+    if (o.lambda_fixed > 0.0) {
+        ctx->lambda = o.lambda_fixed;
+        ctx->power_iters = 0;
+        ctx->power_time = 0.0;
+    } else {
+        st = run_power(ctx);
+        if (st) return st;
+        ctx->power_time = now_s() - t0;
+    }
+    const double lambda = ctx->lambda;
+
+    // ---- origin start, sigma_0 (Section 4.1)
+    CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * n, s));
+    CK(cudaMemsetAsync(ctx->x0, 0, sizeof(double) * n, s));
+    CK(cudaMemsetAsync(ctx->y, 0, sizeof(double) * m, s));
+    CK(cudaMemsetAsync(ctx->y0, 0, sizeof(double) * m, s));
+
+    double sigma = o.sigma0;
+    int64_t k = 0, t = 0, r = 0;
+    int status = HPR_MAX_ITER;
+    double R0 = 0.0, Rprev = 0.0;
+    double last_pobj = 0, last_dobj = 0, last_ep = 0, last_ed = 0, last_gap = 0, last_kkt = 0;
+    double time_1e4 = -1.0;
+    int64_t iters_1e4 = -1;
+    const bool tracing = ctx->trace_n > 0;
+
+    while (k < o.max_iter) {
+        // iterations up to and including the next check
+        const int64_t to_check = o.check_every - (k % o.check_every);
+        const int L = (int)std::min<int64_t>(to_check, o.max_iter - k);
+        const bool first_r0 = (t == 0);
+
+        DevCtl *h = ctx->ctl_h;
+        h->sigma = sigma;
+        h->inv_ls = 1.0 / (lambda * sigma);
+        for (int i = 0; i < L; ++i) {
+            const double tt = (double)(t + i);
+            h->h[2 * i] = 1.0 / (tt + 2.0);
+            h->h[2 * i + 1] = (tt + 1.0) / (tt + 2.0);
+        }
+        CK(cudaMemcpyAsync(ctx->ctl, h, sizeof(DevCtl) + sizeof(double) * 2 * L,
+                           cudaMemcpyHostToDevice, s));
+
+        const bool trace_period = tracing && k < ctx->trace_n;
+        if (trace_period) {
+            for (int i = 0; i < L; ++i) {
+                const bool last = (i == L - 1);
+                const bool r0 = (i == 0 && first_r0);
+                // every traced iteration runs in check mode so that x_bar, y_bar are stored
+                ctx->launches += 2;
+                if (ctx->ntT) k_phase_x<true><<<ctx->ntT, TB, 0, s>>>(xargs(ctx), i);
+                CKL();
+                if (ctx->ntA) k_phase_y<true><<<ctx->ntA, TB, 0, s>>>(yargs(ctx), i);
+                CKL();
+                if (last || r0) {
+                    // residual passes and reductions of a check iteration
+                    DualArgs d;
+                    d.tiles = ctx->tilesT; d.rp = ctx->T_rp; d.ci = ctx->T_ci; d.val = ctx->T_val;
+                    d.ybar = ctx->ybar; d.c = ctx->c_s; d.zbar = ctx->zbar; d.wc = ctx->wc;
+                    d.partials = ctx->partials; d.pstride = ctx->pstride;
+                    if (ctx->ntT) k_check_dual<<<ctx->ntT, TB, 0, s>>>(d);
+                    CKL();
+                    PrimalArgs p;
+                    p.tiles = ctx->tilesA; p.rp = ctx->A_rp; p.ci = ctx->A_ci; p.val = ctx->A_val;
+                    p.xbar = ctx->xbar; p.dx = ctx->dx; p.b = ctx->b_s; p.wr = ctx->wr; p.dy = ctx->dy;
+                    p.partials = ctx->partials; p.pstride = ctx->pstride; p.m1 = (int)ctx->m1;
+                    if (ctx->ntA) k_check_primal<<<ctx->ntA, TB, 0, s>>>(p);
+                    CKL();
+                    ctx->launches += 2;
+                    const int nT = ctx->ntT, nA = ctx->ntA;
+                    st = launch_reduce(ctx, {{Q_DX2, nT}, {Q_XX0, nT}, {Q_CX, nT}, {Q_BND, nT},
+                                             {Q_DY2, nA}, {Q_YY0, nA}, {Q_BY, nA}, {Q_RD, nT},
+                                             {Q_RP, nA}, {Q_CROSS, nA}},
+                                       ctx->scal + (last ? 1 : 0) * NQ);
+                    if (st) return st;
+                }
+                if (!last) {
+                    st = trace_copy(ctx, k + i);
+                    if (st) return st;
+                }
+            }
+        } else if (o.use_graph) {
+            const GraphKey key{L, first_r0 ? 1 : 0};
+            auto itg = ctx->graphs.find(key);
+            if (itg == ctx->graphs.end()) {
+                CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                const int64_t before = ctx->launches;
+                int rr = enqueue_period(ctx, L, first_r0);
+                ctx->graph_launches[key] = ctx->launches - before;
+                ctx->launches = before;
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamEndCapture(s, &g);
+                if (rr) { if (g) cudaGraphDestroy(g); return rr; }
+                if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaStreamEndCapture", __LINE__);
+                cudaGraphExec_t ex = nullptr;
+                e = cudaGraphInstantiate(&ex, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaGraphInstantiate", __LINE__);
+                itg = ctx->graphs.emplace(key, ex).first;
+            }
+            CK(cudaGraphLaunch(itg->second, s));
+            ctx->launches += ctx->graph_launches[key];
+        } else {
+            st = enqueue_period(ctx, L, first_r0);
+            if (st) return st;
+        }
+        CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double) * 2 * NQ, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double elapsed = now_s() - t0;
+
+        const double *S1 = ctx->scal_h + NQ;
+        const double *S0 = (first_r0 && L > 1) ? ctx->scal_h : S1;
+        const int64_t kk = k + L - 1;           // index of the check iteration
+        const int64_t tl = t + L - 1;           // its inner counter
+        if (first_r0 && L > 1) {
+            R0 = merit_from(S0, sigma, lambda);
+            Rprev = R0;
+            hpr_check_record rec{};
+            rec.k = k; rec.r = r; rec.t = 0; rec.kind = 2; rec.cause = 0;
+            rec.sigma = sigma; rec.Rt = R0; rec.R0 = R0; rec.sigma_next = sigma;
+            rec.elapsed_s = elapsed;
+            ctx->checks.push_back(rec);
+        }
+        const bool is_r0 = (tl == 0);
+        const double Rt = merit_from(S1, sigma, lambda);
+        if (is_r0) {
+            R0 = Rt;
+            Rprev = Rt;
+        }
+        // termination test of Section 4.1 in the original space
+        const double bb = ctx->beta_b * ctx->beta_c;
+        const double errp = std::sqrt(S1[Q_RP]) / (1.0 + ctx->norm_b);
+        const double errd = std::sqrt(S1[Q_RD]) / (1.0 + ctx->norm_c);
+        const double pobj = bb * S1[Q_CX];
+        const double dobj = bb * (S1[Q_BY] + S1[Q_BND]);
+        const double gap = std::fabs(dobj - pobj) / (1.0 + std::fabs(pobj) + std::fabs(dobj));
+        const double kkt = std::max(errp, std::max(errd, gap));
+        last_pobj = pobj; last_dobj = dobj; last_ep = errp; last_ed = errd; last_gap = gap; last_kkt = kkt;
+        if (!std::isfinite(kkt) || !std::isfinite(Rt))
+            return fail_arg(ctx, HPR_ERR_NUMERIC, "non-finite residual at iteration " + std::to_string(kk));
+        if (time_1e4 < 0.0 && kkt <= 1e-4) {
+            time_1e4 = elapsed;
+            iters_1e4 = kk + 1;
+        }
+
+        int cause = 0;
+        bool restart = false, stop = false;
+        double sigma_next = sigma, Dx = 0.0, Dy = 0.0;
+        if (kkt <= tol) {
+            stop = true;
+            status = HPR_OK;
+            cause = -1;
+        } else if (kk + 1 < o.max_iter && o.restart && !is_r0) {
+            // restart criteria eq. (restart_1)-(restart_3)
+            if (Rt <= o.alpha1 * R0) cause = 1;
+            else if (Rt <= o.alpha2 * R0 && Rt > Rprev) cause = 2;
+            else if ((double)(tl + 1) >= o.alpha3 * (double)(kk + 1)) cause = 3;
+            Rprev = Rt;
+            restart = cause != 0;
+        }
+        if (restart) {
+            // Algorithm 3 with eq. (sigma_T1!=0)
+            Dx = std::sqrt(S1[Q_XX0]);
+            Dy = std::sqrt(lambda) * std::sqrt(S1[Q_YY0]);
+            const double ratio = errd / errp;
+            if (o.sigma_update && Dx > 1e-16 && Dx < 1e12 && Dy > 1e-16 && Dy < 1e12 &&
+                errp > 0.0 && ratio > 1e-8 && ratio < 1e8)
+                sigma_next = Dx / Dy;
+            else
+                sigma_next = o.sigma_update ? 1.0 : sigma;
+        }
+        {
+            hpr_check_record rec{};
+            rec.k = kk; rec.r = r; rec.t = tl; rec.kind = 1 + (is_r0 ? 2 : 0); rec.cause = cause;
+            rec.sigma = sigma; rec.err_p = errp; rec.err_d = errd; rec.err_gap = gap; rec.kkt = kkt;
+            rec.pobj = pobj; rec.dobj = dobj; rec.Rt = Rt; rec.R0 = R0; rec.sigma_next = sigma_next;
+            rec.Dx = Dx; rec.Dy = Dy; rec.elapsed_s = elapsed;
+            ctx->checks.push_back(rec);
+        }
+        if (o.verbose)
+            fprintf(stderr, "hpr k=%lld r=%lld t=%lld sigma=%.3e kkt=%.3e (p %.2e d %.2e g %.2e) R=%.3e cause=%d %.3fs\n",
+                    (long long)(kk + 1), (long long)r, (long long)tl, sigma, kkt, errp, errd, gap, Rt,
+                    cause, elapsed);
+
+        if (restart) {
+            k_restart<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->xbar, ctx->ybar, ctx->x,
+                                                      ctx->x0, ctx->y, ctx->y0);
+            CKL();
+            ctx->launches += 1;
+            sigma = sigma_next;
+            t = 0;
+            r++;
+        } else {
+            t = tl + 1;
+        }
+        if (tracing && kk < ctx->trace_n) {
+            st = trace_copy(ctx, kk);
+            if (st) return st;
+        }
+        k = kk + 1;
+        if (stop) break;
+        if (o.time_limit_s > 0.0 && elapsed >= o.time_limit_s && k < o.max_iter) {
+            status = HPR_TIME_LIMIT;
+            break;
+        }
+    }
+
+    // output: the last w_bar mapped back to the original LP
+    k_backmap<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->beta_b, ctx->beta_c, ctx->xbar,
+                                              ctx->ybar, ctx->zbar, ctx->Dr, ctx->Dc, ctx->l_o,
+                                              ctx->u_o, ctx->xo, ctx->yo, ctx->zo);
+    CKL();
+    ctx->launches += 1;
+    CK(cudaStreamSynchronize(s));
+    const double total = now_s() - t0;
+
+    hpr_info &I = ctx->info;
+    memset(&I, 0, sizeof I);
+    I.primal_obj = last_pobj; I.dual_obj = last_dobj; I.err_p = last_ep; I.err_d = last_ed;
+    I.err_gap = last_gap; I.kkt = last_kkt; I.sigma = sigma; I.lambda = lambda;
+    I.solve_time_s = total; I.power_time_s = ctx->power_time;
+    I.time_to_1e4_s = time_1e4; I.iters_to_1e4 = iters_1e4;
+    I.iters = k; I.restarts = r; I.power_iters = ctx->power_iters;
+    I.n_checks = (int64_t)ctx->checks.size(); I.launches = ctx->launches; I.status = status;
+    ctx->solved = true;
+    return status;
+}
+
+int hpr_get(const hpr_ctx *cctx, double *x, double *y, double *z, hpr_info *info)
+{
+    if (!cctx) return HPR_ERR_ARG;
+    hpr_ctx *ctx = const_cast<hpr_ctx *>(cctx);
+    if (!ctx->solved) return fail_arg(ctx, HPR_ERR_STATE, "no solve has completed");
+    cudaSetDevice(ctx->device);
+    if (x) CK(cudaMemcpyAsync(x, ctx->xo, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (y) CK(cudaMemcpyAsync(y, ctx->yo, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+    if (z) CK(cudaMemcpyAsync(z, ctx->zo, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (info) *info = ctx->info;
+    return HPR_OK;
+}
+
+int hpr_get_scaling(const hpr_ctx *cctx, double *Dr, double *Dc, double *As_val, double *bs,
+                    double *cs, double *ls, double *us, double *beta)
+{
+    if (!cctx) return HPR_ERR_ARG;
+    hpr_ctx *ctx = const_cast<hpr_ctx *>(cctx);
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    if (Dr) CK(cudaMemcpyAsync(Dr, ctx->Dr, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, s));
+    if (Dc) CK(cudaMemcpyAsync(Dc, ctx->Dc, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, s));
+    if (As_val) CK(cudaMemcpyAsync(As_val, ctx->A_val, sizeof(double) * ctx->nnz, cudaMemcpyDeviceToHost, s));
+    if (bs) CK(cudaMemcpyAsync(bs, ctx->b_s, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, s));
+    if (cs) CK(cudaMemcpyAsync(cs, ctx->c_s, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, s));
+    if (ls) CK(cudaMemcpyAsync(ls, ctx->l_s, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, s));
+    if (us) CK(cudaMemcpyAsync(us, ctx->u_s, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (beta) {
+        beta[0] = ctx->beta_b;
+        beta[1] = ctx->beta_c;
+    }
+    return HPR_OK;
+}
+
+int hpr_get_checks(const hpr_ctx *ctx, hpr_check_record *out, int64_t cap, int64_t *count)
+{
+    if (!ctx) return HPR_ERR_ARG;
+    const int64_t cnt = (int64_t)ctx->checks.size();
+    if (count) *count = cnt;
+    if (out && cap > 0) memcpy(out, ctx->checks.data(), sizeof(hpr_check_record) * (size_t)std::min(cap, cnt));
+    return HPR_OK;
+}
+
+int hpr_get_trace(const hpr_ctx *cctx, int64_t k, double *xbar, double *xhat, double *x,
+                  double *ybar, double *y)
+{
+    if (!cctx) return HPR_ERR_ARG;
+    hpr_ctx *ctx = const_cast<hpr_ctx *>(cctx);
+    if (k < 0 || k >= ctx->trace_written) return fail_arg(ctx, HPR_ERR_STATE, "iteration not traced");
+    cudaSetDevice(ctx->device);
+    const int64_t n = ctx->n, m = ctx->m;
+    const double *rec = ctx->trace + (size_t)k * (size_t)(3 * n + 2 * m);
+    cudaStream_t s = ctx->stream;
+    if (xbar) CK(cudaMemcpyAsync(xbar, rec, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (xhat) CK(cudaMemcpyAsync(xhat, rec + n, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (x) CK(cudaMemcpyAsync(x, rec + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (ybar) CK(cudaMemcpyAsync(ybar, rec + 3 * n, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    if (y) CK(cudaMemcpyAsync(y, rec + 3 * n + m, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return HPR_OK;
+}
+
+int hpr_time_iteration(hpr_ctx *ctx, int64_t reps, double *ms_x, double *ms_y, double *ms_iter)
+{
+    if (!ctx || reps < 1) return HPR_ERR_ARG;
+    if (!ctx->solved) return fail_arg(ctx, HPR_ERR_STATE, "no solve has completed");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    // coefficients of a mid-run Halpern step; the timing does not depend on them
+    DevCtl *h = ctx->ctl_h;
+    h->sigma = ctx->info.sigma > 0.0 ? ctx->info.sigma : 1.0;
+    h->inv_ls = 1.0 / (ctx->lambda * h->sigma);
+    h->h[0] = 1.0 / 1002.0;
+    h->h[1] = 1001.0 / 1002.0;
+    CK(cudaMemcpyAsync(ctx->ctl, h, sizeof(DevCtl), cudaMemcpyHostToDevice, s));
+    cudaEvent_t ev[3];
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    double tx = 0.0, ty = 0.0;
+    float a = 0.f, b = 0.f;
+    int rc = HPR_OK;
+    for (int64_t r = 0; r < reps && rc == HPR_OK; ++r) {
+        cudaEventRecord(ev[0], s);
+        if (ctx->ntT) k_phase_x<false><<<ctx->ntT, TB, 0, s>>>(xargs(ctx), 0);
+        cudaEventRecord(ev[1], s);
+        if (ctx->ntA) k_phase_y<false><<<ctx->ntA, TB, 0, s>>>(yargs(ctx), 0);
+        cudaEventRecord(ev[2], s);
+        cudaError_t e = cudaEventSynchronize(ev[2]);
+        if (e != cudaSuccess) { rc = fail_cuda(ctx, e, "hpr_time_iteration", __LINE__); break; }
+        cudaEventElapsedTime(&a, ev[0], ev[1]);
+        cudaEventElapsedTime(&b, ev[1], ev[2]);
+        tx += a;
+        ty += b;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc) return rc;
+    if (ms_x) *ms_x = tx / (double)reps;
+    if (ms_y) *ms_y = ty / (double)reps;
+    if (ms_iter) *ms_iter = (tx + ty) / (double)reps;
+    return HPR_OK;
+}
+
+const char *hpr_last_error(const hpr_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_static_err;
+}
+
+const char *hpr_status_str(int s)
+{
+    switch (s) {
+    case HPR_OK: return "HPR_OK";
+    case HPR_MAX_ITER: return "HPR_MAX_ITER";
+    case HPR_TIME_LIMIT: return "HPR_TIME_LIMIT";
+    case HPR_ERR_ARG: return "HPR_ERR_ARG";
+    case HPR_ERR_ZERO_MATRIX: return "HPR_ERR_ZERO_MATRIX";
+    case HPR_ERR_NOMEM: return "HPR_ERR_NOMEM";
+    case HPR_ERR_CUDA: return "HPR_ERR_CUDA";
+    case HPR_ERR_DEVICE_TIMEOUT: return "HPR_ERR_DEVICE_TIMEOUT";
+    case HPR_ERR_NUMERIC: return "HPR_ERR_NUMERIC";
+    case HPR_ERR_STATE: return "HPR_ERR_STATE";
+    case HPR_ERR_NO_DEVICE: return "HPR_ERR_NO_DEVICE";
+    default: return "HPR_UNKNOWN";
+    }
+}
+
+void hpr_destroy(hpr_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    delete ctx;
+}
+
+}  // extern "C"
