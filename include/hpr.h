@@ -163,6 +163,34 @@ int hpr_get_trace(const hpr_ctx *ctx, int64_t k, double *xbar, double *xhat, dou
  * pointer may be NULL.  HPR_ERR_STATE before the first solve. */
 int hpr_time_iteration(hpr_ctx *ctx, int64_t reps, double *ms_x, double *ms_y, double *ms_iter);
 
+/* Allocation-free power method (the paper has no counterpart: it is an extra entry
+ * point of this library).  For callers that are not allowed to allocate device memory
+ * themselves -- code that runs under a memory budget or pool owned by someone else
+ * (an inference server, a framework's caching allocator) or that must not call
+ * cudaMalloc at that point -- and that already hold the LP matrix on the device.
+ * Computes the same lambda_1(A A^*) as hpr_power on the given matrix, but allocates
+ * nothing: its per-CTA partial sums, reduced scalars and control block live in one
+ * fixed array of 131,456 bytes in device global memory that is part of the library
+ * and stays allocated on every device that loaded the library until the process exits.
+ *   m, n            rows and columns of A; each in [1, 2^31 - 2] (otherwise HPR_ERR_ARG)
+ *   A_*, At_*       DEVICE CSR arrays (32-bit) of A (m rows) and of its transpose
+ *                   (n rows), column indices sorted within rows
+ *   seed, max_iter, tol   as in hpr_options (power method of Section 4.1)
+ *   u (m), s (n)    DEVICE output buffers: the final unit vector u and s = A^T u of
+ *                   the last step (both are overwritten during the iteration)
+ *   cuda_stream     cudaStream_t to run on (NULL: the legacy default stream)
+ *   lambda, iters   HOST outputs (may be NULL)
+ * The call synchronises its stream every 16 power steps.  The first call on a device
+ * looks up the array's device address with that device current; make that first call
+ * before any stream capture.  All calls on a device share the array, so calls that
+ * overlap on the GPU (other threads, other streams) race and must be serialised by the
+ * caller.  Returns HPR_OK, HPR_ERR_ARG, HPR_ERR_NUMERIC or HPR_ERR_CUDA; the detail is
+ * in hpr_last_error(NULL). */
+int hpr_power_noalloc(int64_t m, int64_t n, const int32_t *A_row_ptr, const int32_t *A_col_idx,
+                      const double *A_val, const int32_t *At_row_ptr, const int32_t *At_col_idx,
+                      const double *At_val, uint64_t seed, int64_t max_iter, double tol,
+                      double *u, double *s, void *cuda_stream, double *lambda, int64_t *iters);
+
 /* Detail of the last error of ctx (a static string when ctx is NULL). */
 const char *hpr_last_error(const hpr_ctx *ctx);
 

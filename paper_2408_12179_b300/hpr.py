@@ -82,6 +82,11 @@ SIGNATURES = {
                                       ctypes.c_int64, _I64]),
     "hpr_get_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _D, _D, _D, _D, _D]),
     "hpr_time_iteration": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _D, _D, _D]),
+    "hpr_power_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                         ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, _D, _I64]),
     "hpr_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hpr_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "hpr_destroy": (None, [ctypes.c_void_p]),
@@ -225,6 +230,19 @@ def hpr_time_iteration(ctx, reps: int):
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().hpr_time_iteration(ctx, int(reps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), ctx)
     return a.value, b.value, c.value
+
+
+def hpr_power_noalloc(m, n, A_ptrs, At_ptrs, seed, max_iter, tol, u_ptr, s_ptr, stream=None):
+    """Allocation-free power method on device CSR arrays given as raw device addresses
+    (A_ptrs / At_ptrs = (row_ptr, col_idx, val)); u_ptr (m doubles) and s_ptr (n) are
+    device output buffers.  Returns (lambda, iterations)."""
+    lam = ctypes.c_double()
+    it = ctypes.c_int64()
+    code = load().hpr_power_noalloc(int(m), int(n), *A_ptrs, *At_ptrs, int(seed), int(max_iter),
+                                    float(tol), u_ptr, s_ptr, stream, ctypes.byref(lam),
+                                    ctypes.byref(it))
+    _check(code, None)
+    return lam.value, it.value
 
 
 def hpr_destroy(ctx):
