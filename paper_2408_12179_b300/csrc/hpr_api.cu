@@ -1,7 +1,8 @@
 // C ABI and host runtime of the B300 HPR-LP solver; declarations in include/hpr.h.
 //
 // Host responsibilities: validate the LP, assemble A = [A1; A2], build the explicit
-// CSR of A^T (stable counting sort) and the tile schedules of both matrices, drive
+// CSR of A^T (stable counting sort) and the sliced-ELL layouts of both matrices with
+// their row / column renumbering (rows by decreasing length, stable), drive
 // the preprocessing / power-method / iteration kernels, and take the scalar decisions
 // of Algorithm 2 (termination, restart criteria of Section 3.1, Algorithm 3) once per
 // check period from ~16 reduced FP64 scalars.  Every vector operation of the method
@@ -41,6 +42,20 @@ struct GraphKey {
 
 }  // namespace
 
+struct Grids {
+    int X, Xc, Y, Yc, Dual, Primal, Norm;   // grid of each sliced-ELL kernel (all CTAs resident)
+};
+
+// one matrix in the sliced-ELL layout (device arrays; see k_sell)
+struct SellDev {
+    int rows = 0, nslices = 0;
+    int64_t entries = 0;          // stored entries (nonzeros + padding)
+    int *srow = nullptr, *sptr = nullptr, *wstart = nullptr, *col = nullptr;
+    unsigned char *slg = nullptr;
+    double *val = nullptr;
+    int *src = nullptr;           // CSR position of each stored entry (-1: padding)
+};
+
 struct hpr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -54,13 +69,21 @@ struct hpr_ctx {
     double *A_val = nullptr;
     int *T_rp = nullptr, *T_ci = nullptr, *T_perm = nullptr;
     double *T_val = nullptr;
-    int *tilesA = nullptr, *tilesT = nullptr;
-    int ntA = 0, ntT = 0;
+    SellDev SA, ST;               // A and A^T in the renumbered sliced-ELL layout
+    int *perm_r = nullptr;        // renumbered row i of A is original row perm_r[i]
+    int *perm_c = nullptr;        // renumbered column j is original column perm_c[j]
+    unsigned char *ineq = nullptr;// renumbered row i belongs to A2 (m2 block)
+    Grids grids{};
+    int num_sms = 0;
 
     // vectors (device)
+    // preprocessing results in the original order
     double *Dr = nullptr, *Dc = nullptr, *wr = nullptr, *wc = nullptr;
     double *b_s = nullptr, *c_s = nullptr, *l_s = nullptr, *u_s = nullptr;
     double *l_o = nullptr, *u_o = nullptr;
+    // the same in the renumbered order used by the iteration
+    double *bp = nullptr, *cp = nullptr, *lp = nullptr, *up = nullptr, *wrp = nullptr, *wcp = nullptr;
+    double *unperm = nullptr;     // n + m scratch for copying iterates out in the original order
     double *x = nullptr, *x0 = nullptr, *xhat = nullptr, *xbar = nullptr, *zbar = nullptr,
            *dx = nullptr;
     double *y = nullptr, *y0 = nullptr, *ybar = nullptr, *dy = nullptr;
@@ -154,23 +177,103 @@ int grid_for(int64_t n, int threads = 256, int cap = 148 * 16)
     return (int)g;
 }
 
-// Tile schedule: consecutive rows, at most TILE_ROWS rows and TILE_NNZ nonzeros per
-// tile; a row longer than TILE_NNZ is a tile of its own.
-std::vector<int> build_tiles(const std::vector<int> &rp, int rows)
+// Renumbering by decreasing row length, stable (rows of equal length keep their order,
+// so locality inside a length class survives): perm[new] = old.
+std::vector<int> order_by_length(const std::vector<int> &rp, int rows)
 {
-    std::vector<int> t;
-    t.push_back(0);
-    int r = 0;
-    while (r < rows) {
-        const int start = r;
-        if (rp[r + 1] - rp[r] > TILE_NNZ) {
-            ++r;
-        } else {
-            while (r < rows && r - start < TILE_ROWS && rp[r + 1] - rp[start] <= TILE_NNZ) ++r;
+    int maxlen = 0;
+    for (int i = 0; i < rows; ++i) maxlen = std::max(maxlen, rp[(size_t)i + 1] - rp[(size_t)i]);
+    std::vector<int> cnt((size_t)maxlen + 2, 0);
+    for (int i = 0; i < rows; ++i) cnt[(size_t)(maxlen - (rp[(size_t)i + 1] - rp[(size_t)i]))]++;
+    int acc = 0;
+    for (auto &v : cnt) { const int c = v; v = acc; acc += c; }
+    std::vector<int> perm((size_t)rows);
+    for (int i = 0; i < rows; ++i) perm[(size_t)cnt[(size_t)(maxlen - (rp[(size_t)i + 1] - rp[(size_t)i]))]++] = i;
+    return perm;
+}
+
+// Sliced-ELL layout of a CSR matrix (rows in the order perm, longest first; columns
+// renamed by icol): host index arrays; the values are gathered on the GPU through `src`.
+// Rows are taken in groups of 32; a group uses L lanes per row, L the smallest power of
+// two that keeps its widest slice within SELL_STEPS steps (L <= 32), and is stored as L
+// slices of 32 / L rows.  Groups are then split over `runs` warps in contiguous runs of
+// about equal cost.
+constexpr int SELL_STEPS = 40;
+
+struct SellHost {
+    int nslices = 0;
+    std::vector<int> srow, sptr, col, src, wstart;
+    std::vector<unsigned char> slg;
+};
+
+SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int rows,
+                    const std::vector<int> &perm, const std::vector<int> &icol, int runs)
+{
+    SellHost h;
+    auto len = [&](int i) { return rp[(size_t)perm[(size_t)i] + 1] - rp[(size_t)perm[(size_t)i]]; };
+    std::vector<double> scost;       // cost of each slice (epilogue share included)
+    std::vector<int> gfirst;         // first slice of each group
+    h.srow.push_back(0);
+    h.sptr.push_back(0);
+    for (int g0 = 0; g0 < rows; g0 += 32) {
+        const int g1 = std::min(rows, g0 + 32);
+        const int lmax = len(g0);
+        int lg = 0;
+        while (lg < 5 && (lmax + (1 << lg) - 1) / (1 << lg) > SELL_STEPS) ++lg;
+        const int L = 1 << lg, per = 32 / L;
+        gfirst.push_back(h.nslices);
+        for (int r = g0; r < g1; r += per) {
+            const int r1 = std::min(g1, r + per);
+            const int steps = (len(r) + L - 1) / L;
+            const size_t base = h.col.size();
+            h.col.resize(base + (size_t)32 * steps, 0);
+            h.src.resize(base + (size_t)32 * steps, -1);
+            for (int q = 0; q < r1 - r; ++q) {
+                const int orow = perm[(size_t)(r + q)];
+                for (int e = 0, p = rp[(size_t)orow]; p < rp[(size_t)orow + 1]; ++p, ++e) {
+                    const size_t at = base + (size_t)(e / L) * 32 + (size_t)(q * L + e % L);
+                    h.col[at] = icol[(size_t)ci[(size_t)p]];
+                    h.src[at] = p;
+                }
+            }
+            h.slg.push_back((unsigned char)lg);
+            h.srow.push_back(r1);
+            h.sptr.push_back((int)h.col.size());
+            h.nslices++;
+            scost.push_back((double)steps + 2.0 + lg + 8.0 * (r1 - r) / 32.0);
         }
-        t.push_back(r);
     }
-    return t;
+    gfirst.push_back(h.nslices);
+    // work units: a light group whole, a heavy group (costlier than an average run) by
+    // slice; then contiguous runs of units of about equal cost
+    double total = 0.0;
+    for (double c : scost) total += c;
+    const double target = total / (double)runs;
+    std::vector<int> ustart;
+    std::vector<double> ucost;
+    for (size_t g = 0; g + 1 < gfirst.size(); ++g) {
+        double gc = 0.0;
+        for (int sl = gfirst[g]; sl < gfirst[g + 1]; ++sl) gc += scost[(size_t)sl];
+        if (gc <= target) {
+            ustart.push_back(gfirst[g]);
+            ucost.push_back(gc);
+        } else {
+            for (int sl = gfirst[g]; sl < gfirst[g + 1]; ++sl) {
+                ustart.push_back(sl);
+                ucost.push_back(scost[(size_t)sl]);
+            }
+        }
+    }
+    ustart.push_back(h.nslices);
+    h.wstart.assign((size_t)runs + 1, h.nslices);
+    h.wstart[0] = 0;
+    double acc = 0.0;
+    int wi = 1;
+    for (size_t u = 0; u + 1 < ustart.size() && wi < runs; ++u) {
+        acc += ucost[u];
+        while (wi < runs && acc >= total * (double)wi / (double)runs) h.wstart[(size_t)wi++] = ustart[u + 1];
+    }
+    return h;
 }
 
 int validate_block(hpr_ctx *ctx, const hpr_csr *B, const char *name, int64_t *rows, int64_t *cols)
@@ -213,7 +316,10 @@ void free_all(hpr_ctx *c)
     if (c->pow_graph) cudaGraphExecDestroy(c->pow_graph);
     c->pow_graph = nullptr;
     void *dev[] = {c->A_rp, c->A_ci, c->A_val, c->T_rp, c->T_ci, c->T_perm, c->T_val,
-                   c->tilesA, c->tilesT, c->Dr, c->Dc, c->wr, c->wc, c->b_s, c->c_s,
+                   c->SA.srow, c->SA.sptr, c->SA.wstart, c->SA.slg, c->SA.col, c->SA.val, c->SA.src,
+                   c->ST.srow, c->ST.sptr, c->ST.wstart, c->ST.slg, c->ST.col, c->ST.val, c->ST.src,
+                   c->perm_r, c->perm_c, c->ineq, c->bp, c->cp, c->lp, c->up, c->wrp, c->wcp,
+                   c->unperm, c->Dr, c->Dc, c->wr, c->wc, c->b_s, c->c_s,
                    c->l_s, c->u_s, c->l_o, c->u_o, c->x, c->x0, c->xhat, c->xbar,
                    c->zbar, c->dx, c->y, c->y0, c->ybar, c->dy, c->xo, c->yo, c->zo,
                    c->partials, c->scal, c->ctl, c->pctl, c->trace};
@@ -253,59 +359,100 @@ int launch_reduce(hpr_ctx *ctx, const std::vector<std::pair<int, int>> &qc, doub
     return HPR_OK;
 }
 
-XArgs xargs(hpr_ctx *c)
+SellArgs sell_of(hpr_ctx *ctx, const SellDev &d, const int *skip = nullptr)
 {
-    XArgs a;
-    a.tiles = c->tilesT; a.rp = c->T_rp; a.ci = c->T_ci; a.val = c->T_val; a.y = c->y;
-    a.c = c->c_s; a.l = c->l_s; a.u = c->u_s; a.x0 = c->x0; a.x = c->x; a.xhat = c->xhat;
-    a.xbar = c->xbar; a.zbar = c->zbar; a.dx = c->dx; a.partials = c->partials;
-    a.pstride = c->pstride; a.ctl = c->ctl;
+    (void)ctx;
+    SellArgs a;
+    a.rows = d.rows; a.nslices = d.nslices; a.srow = d.srow; a.sptr = d.sptr; a.slg = d.slg;
+    a.wstart = d.wstart; a.val = d.val; a.col = d.col; a.skip = skip;
     return a;
 }
 
-YArgs yargs(hpr_ctx *c)
+// every k_sell instance runs on the same grid (the slice-to-warp table depends on it):
+// SELL_CTAS_PER_SM CTAs of 256 threads per SM, all resident (launch bounds)
+template <class E>
+int setup_kernel(hpr_ctx *ctx, int *grid)
 {
-    YArgs a;
-    a.tiles = c->tilesA; a.rp = c->A_rp; a.ci = c->A_ci; a.val = c->A_val; a.xhat = c->xhat;
-    a.b = c->b_s; a.y0 = c->y0; a.y = c->y; a.ybar = c->ybar; a.dy = c->dy;
-    a.partials = c->partials; a.pstride = c->pstride; a.m1 = (int)c->m1; a.ctl = c->ctl;
-    return a;
-}
-
-// one HPR iteration (phase X then phase Y); a check iteration also runs the two
-// residual passes and reduces everything into scal slot `slot`
-int enqueue_iteration(hpr_ctx *ctx, int it, bool check, int slot)
-{
-    ctx->launches += (ctx->ntT ? 1 : 0) + (ctx->ntA ? 1 : 0);
-    if (check) {
-        ctx->launches += (ctx->ntT ? 1 : 0) + (ctx->ntA ? 1 : 0);
-        if (ctx->ntT) k_phase_x<true><<<ctx->ntT, TB, 0, ctx->stream>>>(xargs(ctx), it);
-        CKL();
-        if (ctx->ntA) k_phase_y<true><<<ctx->ntA, TB, 0, ctx->stream>>>(yargs(ctx), it);
-        CKL();
-        DualArgs d;
-        d.tiles = ctx->tilesT; d.rp = ctx->T_rp; d.ci = ctx->T_ci; d.val = ctx->T_val;
-        d.ybar = ctx->ybar; d.c = ctx->c_s; d.zbar = ctx->zbar; d.wc = ctx->wc;
-        d.partials = ctx->partials; d.pstride = ctx->pstride;
-        if (ctx->ntT) k_check_dual<<<ctx->ntT, TB, 0, ctx->stream>>>(d);
-        CKL();
-        PrimalArgs p;
-        p.tiles = ctx->tilesA; p.rp = ctx->A_rp; p.ci = ctx->A_ci; p.val = ctx->A_val;
-        p.xbar = ctx->xbar; p.dx = ctx->dx; p.b = ctx->b_s; p.wr = ctx->wr; p.dy = ctx->dy;
-        p.partials = ctx->partials; p.pstride = ctx->pstride; p.m1 = (int)ctx->m1;
-        if (ctx->ntA) k_check_primal<<<ctx->ntA, TB, 0, ctx->stream>>>(p);
-        CKL();
-        const int nT = ctx->ntT, nA = ctx->ntA;
-        return launch_reduce(ctx, {{Q_DX2, nT}, {Q_XX0, nT}, {Q_CX, nT}, {Q_BND, nT},
-                                   {Q_DY2, nA}, {Q_YY0, nA}, {Q_BY, nA}, {Q_RD, nT},
-                                   {Q_RP, nA}, {Q_CROSS, nA}},
-                             ctx->scal + slot * NQ);
-    }
-    if (ctx->ntT) k_phase_x<false><<<ctx->ntT, TB, 0, ctx->stream>>>(xargs(ctx), it);
-    CKL();
-    if (ctx->ntA) k_phase_y<false><<<ctx->ntA, TB, 0, ctx->stream>>>(yargs(ctx), it);
-    CKL();
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sell<E>, TB, 0));
+    if (per_sm < SELL_CTAS_PER_SM) return fail_arg(ctx, HPR_ERR_CUDA, "sliced-ELL kernel does not fit its CTAs on an SM");
+    *grid = SELL_CTAS_PER_SM * ctx->num_sms;
     return HPR_OK;
+}
+
+template <class E>
+int launch_sell(hpr_ctx *ctx, const SellDev &M, int grid, const E &e, const int *skip = nullptr)
+{
+    if (M.rows == 0) return HPR_OK;
+    k_sell<E><<<grid, TB, 0, ctx->stream>>>(sell_of(ctx, M, skip), e);
+    CKL();
+    ctx->launches += 1;
+    return HPR_OK;
+}
+
+template <bool CHECK>
+EpiX<CHECK> epi_x(hpr_ctx *c, int it)
+{
+    EpiX<CHECK> e{};
+    e.xa = c->y; e.xb = c->y;
+    e.q[0] = Q_DX2; e.q[1] = Q_XX0; e.q[2] = Q_CX; e.q[3] = Q_BND;
+    e.partials = c->partials; e.pstride = c->pstride;
+    e.c = c->cp; e.l = c->lp; e.u = c->up; e.x0 = c->x0;
+    e.x = c->x; e.xhat = c->xhat; e.xbar = c->xbar; e.zbar = c->zbar; e.dx = c->dx;
+    e.ctl = c->ctl; e.it = it;
+    return e;
+}
+
+template <bool CHECK>
+EpiY<CHECK> epi_y(hpr_ctx *c, int it)
+{
+    EpiY<CHECK> e{};
+    e.xa = c->xhat; e.xb = c->xhat;
+    e.q[0] = Q_DY2; e.q[1] = Q_YY0; e.q[2] = Q_BY;
+    e.partials = c->partials; e.pstride = c->pstride;
+    e.b = c->bp; e.y0 = c->y0; e.y = c->y; e.ybar = c->ybar; e.dy = c->dy;
+    e.ctl = c->ctl; e.it = it; e.ineq = c->ineq;
+    return e;
+}
+
+EpiNorm epi_norm(hpr_ctx *c, const double *xin, double *out, int q)
+{
+    EpiNorm e{};
+    e.xa = xin; e.xb = xin; e.q[0] = q; e.partials = c->partials; e.pstride = c->pstride; e.out = out;
+    return e;
+}
+
+// one HPR iteration (phase X then phase Y).  store: the phases also store x_bar, z_bar,
+// y_bar, x - x_bar, y - y_bar; check: the two residual passes run and every check
+// quantity is reduced into scal slot `slot`.
+int enqueue_iteration(hpr_ctx *ctx, int it, bool store, bool check, int slot)
+{
+    int st;
+    const Grids &g = ctx->grids;
+    if (store || check) {
+        if ((st = launch_sell(ctx, ctx->ST, g.Xc, epi_x<true>(ctx, it)))) return st;
+        if ((st = launch_sell(ctx, ctx->SA, g.Yc, epi_y<true>(ctx, it)))) return st;
+    } else {
+        if ((st = launch_sell(ctx, ctx->ST, g.X, epi_x<false>(ctx, it)))) return st;
+        if ((st = launch_sell(ctx, ctx->SA, g.Y, epi_y<false>(ctx, it)))) return st;
+    }
+    if (!check) return HPR_OK;
+    EpiDual d{};
+    d.xa = ctx->ybar; d.xb = ctx->ybar; d.q[0] = Q_RD;
+    d.partials = ctx->partials; d.pstride = ctx->pstride;
+    d.c = ctx->cp; d.zbar = ctx->zbar; d.wc = ctx->wcp;
+    if ((st = launch_sell(ctx, ctx->ST, g.Dual, d))) return st;
+    EpiPrimal p{};
+    p.xa = ctx->xbar; p.xb = ctx->dx; p.q[0] = Q_RP; p.q[1] = Q_CROSS;
+    p.partials = ctx->partials; p.pstride = ctx->pstride;
+    p.b = ctx->bp; p.wr = ctx->wrp; p.dy = ctx->dy; p.ineq = ctx->ineq;
+    if ((st = launch_sell(ctx, ctx->SA, g.Primal, p))) return st;
+    const int nX = ctx->ST.rows ? g.Xc : 0, nY = ctx->SA.rows ? g.Yc : 0;
+    const int nD = ctx->ST.rows ? g.Dual : 0, nP = ctx->SA.rows ? g.Primal : 0;
+    return launch_reduce(ctx, {{Q_DX2, nX}, {Q_XX0, nX}, {Q_CX, nX}, {Q_BND, nX},
+                               {Q_DY2, nY}, {Q_YY0, nY}, {Q_BY, nY}, {Q_RD, nD},
+                               {Q_RP, nP}, {Q_CROSS, nP}},
+                         ctx->scal + slot * NQ);
 }
 
 int enqueue_period(hpr_ctx *ctx, int L, bool first_r0)
@@ -313,7 +460,7 @@ int enqueue_period(hpr_ctx *ctx, int L, bool first_r0)
     for (int i = 0; i < L; ++i) {
         const bool last = (i == L - 1);
         const bool r0 = (i == 0 && first_r0);
-        int s = enqueue_iteration(ctx, i, last || r0, last ? 1 : 0);
+        int s = enqueue_iteration(ctx, i, last || r0, last || r0, last ? 1 : 0);
         if (s != HPR_OK) return s;
     }
     return HPR_OK;
@@ -358,7 +505,8 @@ int run_power(hpr_ctx *ctx)
     const int gm = (int)((m + TB - 1) / TB);
     // u (m) in dy, s = A^T u (n) in dx, w = A s (m) in ybar
     double *u = ctx->dy, *s = ctx->dx, *w = ctx->ybar;
-    k_pow_start<<<gm, TB, 0, ctx->stream>>>((int)m, ctx->opt.seed, u, ctx->partials, ctx->pstride);
+    k_pow_start<<<gm, TB, 0, ctx->stream>>>((int)m, ctx->opt.seed, ctx->perm_r, u, ctx->partials,
+                                             ctx->pstride);
     CKL();
     int st = launch_reduce(ctx, {{Q_V2, gm}}, ctx->scal);
     if (st) return st;
@@ -376,22 +524,15 @@ int run_power(hpr_ctx *ctx)
 
     auto enqueue_steps = [&](int steps) -> int {
         for (int k = 0; k < steps; ++k) {
-            SpmvNormArgs a;
-            a.tiles = ctx->tilesT; a.rp = ctx->T_rp; a.ci = ctx->T_ci; a.val = ctx->T_val;
-            a.xin = u; a.out = s; a.partials = ctx->partials; a.pstride = ctx->pstride;
-            a.q = Q_S2; a.pc = ctx->pctl;
-            if (ctx->ntT) k_spmv_norm<<<ctx->ntT, TB, 0, ctx->stream>>>(a);
-            CKL();
-            int r = launch_reduce(ctx, {{Q_S2, ctx->ntT}}, ctx->scal, &ctx->pctl->done);
+            int r = launch_sell(ctx, ctx->ST, ctx->grids.Norm, epi_norm(ctx, u, s, Q_S2), &ctx->pctl->done);
+            if (r) return r;
+            r = launch_reduce(ctx, {{Q_S2, ctx->ST.rows ? ctx->grids.Norm : 0}}, ctx->scal, &ctx->pctl->done);
             if (r) return r;
             k_pow_after_s<<<1, 1, 0, ctx->stream>>>(ctx->pctl, ctx->scal);
             CKL();
-            SpmvNormArgs b = a;
-            b.tiles = ctx->tilesA; b.rp = ctx->A_rp; b.ci = ctx->A_ci; b.val = ctx->A_val;
-            b.xin = s; b.out = w; b.q = Q_W2;
-            if (ctx->ntA) k_spmv_norm<<<ctx->ntA, TB, 0, ctx->stream>>>(b);
-            CKL();
-            r = launch_reduce(ctx, {{Q_W2, ctx->ntA}}, ctx->scal, &ctx->pctl->done);
+            r = launch_sell(ctx, ctx->SA, ctx->grids.Norm, epi_norm(ctx, s, w, Q_W2), &ctx->pctl->done);
+            if (r) return r;
+            r = launch_reduce(ctx, {{Q_W2, ctx->SA.rows ? ctx->grids.Norm : 0}}, ctx->scal, &ctx->pctl->done);
             if (r) return r;
             k_pow_after_w<<<1, 1, 0, ctx->stream>>>(ctx->pctl, ctx->scal);
             CKL();
@@ -425,7 +566,7 @@ int run_power(hpr_ctx *ctx)
             ctx->launches += (int64_t)BATCH * 8;
             CK(cudaGraphLaunch(ctx->pow_graph, ctx->stream));
         } else {
-            ctx->launches += (int64_t)BATCH * 6;   // the 2 reductions count themselves
+            ctx->launches += (int64_t)BATCH * 4;   // the 2 SpMVs and 2 reductions count themselves
             int r = enqueue_steps(BATCH);
             if (r) return r;
         }
@@ -481,14 +622,56 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
                 tperm[(size_t)q] = p;
             }
     }
-    std::vector<int> tA = build_tiles(rp, (int)m), tT = build_tiles(trp, (int)n);
-    ctx->ntA = (int)tA.size() - 1;
-    ctx->ntT = (int)tT.size() - 1;
-    ctx->pstride = std::max({ctx->ntA, ctx->ntT, (int)((std::max(m, n) + TB - 1) / TB), 1});
+    // renumbering and sliced-ELL layouts of A (rows by length) and A^T (columns by length)
+    std::vector<int> pr = order_by_length(rp, (int)m), pc = order_by_length(trp, (int)n);
+    std::vector<int> ipr((size_t)m), ipc((size_t)n);
+    for (int64_t i = 0; i < m; ++i) ipr[(size_t)pr[(size_t)i]] = (int)i;
+    for (int64_t j = 0; j < n; ++j) ipc[(size_t)pc[(size_t)j]] = (int)j;
+    const int warps = SELL_CTAS_PER_SM * ctx->num_sms * (TB / 32);
+    SellHost hA = build_sell(rp, ci, (int)m, pr, ipc, warps);
+    SellHost hT = build_sell(trp, tci, (int)n, pc, ipr, warps);
+    std::vector<unsigned char> ineq((size_t)m);
+    for (int64_t i = 0; i < m; ++i) ineq[(size_t)i] = pr[(size_t)i] >= m1 ? 1 : 0;
+    {
+        Grids &g = ctx->grids;
+        int r;
+        if ((r = setup_kernel<EpiX<false>>(ctx, &g.X))) return r;
+        if ((r = setup_kernel<EpiX<true>>(ctx, &g.Xc))) return r;
+        if ((r = setup_kernel<EpiY<false>>(ctx, &g.Y))) return r;
+        if ((r = setup_kernel<EpiY<true>>(ctx, &g.Yc))) return r;
+        if ((r = setup_kernel<EpiDual>(ctx, &g.Dual))) return r;
+        if ((r = setup_kernel<EpiPrimal>(ctx, &g.Primal))) return r;
+        if ((r = setup_kernel<EpiNorm>(ctx, &g.Norm))) return r;
+        ctx->pstride = std::max({g.X, g.Xc, g.Y, g.Yc, g.Dual, g.Primal, g.Norm,
+                                 (int)((std::max(m, n) + TB - 1) / TB), 1});
+    }
+    auto upload_sell = [&](SellDev &D, const SellHost &H, int rows) -> int {
+        D.rows = rows; D.nslices = H.nslices;
+        D.entries = (int64_t)H.col.size();
+        DALLOC(D.srow, (int64_t)H.srow.size()); DALLOC(D.sptr, (int64_t)H.sptr.size());
+        DALLOC(D.wstart, (int64_t)H.wstart.size()); DALLOC(D.slg, (int64_t)H.slg.size());
+        DALLOC(D.col, D.entries); DALLOC(D.val, D.entries); DALLOC(D.src, D.entries);
+        CK(cudaMemcpyAsync(D.srow, H.srow.data(), sizeof(int) * H.srow.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(D.sptr, H.sptr.data(), sizeof(int) * H.sptr.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(D.wstart, H.wstart.data(), sizeof(int) * H.wstart.size(), cudaMemcpyHostToDevice, ctx->stream));
+        if (!H.slg.empty())
+            CK(cudaMemcpyAsync(D.slg, H.slg.data(), H.slg.size(), cudaMemcpyHostToDevice, ctx->stream));
+        if (D.entries) {
+            CK(cudaMemcpyAsync(D.col, H.col.data(), sizeof(int) * H.col.size(), cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(D.src, H.src.data(), sizeof(int) * H.src.size(), cudaMemcpyHostToDevice, ctx->stream));
+        }
+        return HPR_OK;
+    };
 
+    int st0;
     DALLOC(ctx->A_rp, m + 1); DALLOC(ctx->A_ci, nnz); DALLOC(ctx->A_val, nnz);
     DALLOC(ctx->T_rp, n + 1); DALLOC(ctx->T_ci, nnz); DALLOC(ctx->T_perm, nnz); DALLOC(ctx->T_val, nnz);
-    DALLOC(ctx->tilesA, ctx->ntA + 1); DALLOC(ctx->tilesT, ctx->ntT + 1);
+    if ((st0 = upload_sell(ctx->SA, hA, (int)m))) return st0;
+    if ((st0 = upload_sell(ctx->ST, hT, (int)n))) return st0;
+    DALLOC(ctx->perm_r, m); DALLOC(ctx->perm_c, n); DALLOC(ctx->ineq, m);
+
+    DALLOC(ctx->bp, m); DALLOC(ctx->wrp, m); DALLOC(ctx->cp, n); DALLOC(ctx->lp, n); DALLOC(ctx->up, n);
+    DALLOC(ctx->wcp, n); DALLOC(ctx->unperm, n + m);
     DALLOC(ctx->Dr, m); DALLOC(ctx->Dc, n); DALLOC(ctx->wr, m); DALLOC(ctx->wc, n);
     DALLOC(ctx->b_s, m); DALLOC(ctx->c_s, n); DALLOC(ctx->l_s, n); DALLOC(ctx->u_s, n);
     DALLOC(ctx->l_o, n); DALLOC(ctx->u_o, n);
@@ -511,8 +694,9 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     CK(cudaMemcpyAsync(ctx->T_rp, trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->T_ci, tci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->T_perm, tperm.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->tilesA, tA.data(), sizeof(int) * tA.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->tilesT, tT.data(), sizeof(int) * tT.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->perm_r, pr.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->perm_c, pc.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->ineq, ineq.data(), m, cudaMemcpyHostToDevice, s));
     if (m1) CK(cudaMemcpyAsync(ctx->b_s, b1, sizeof(double) * m1, cudaMemcpyHostToDevice, s));
     if (m2) CK(cudaMemcpyAsync(ctx->b_s + m1, b2, sizeof(double) * m2, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->c_s, c, sizeof(double) * n, cudaMemcpyHostToDevice, s));
@@ -560,6 +744,15 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
                                                               ctx->Dr, ctx->Dc, ctx->b_s, ctx->c_s,
                                                               ctx->l_s, ctx->u_s, ctx->wr, ctx->wc);
     CKL();
+    // the iteration's copies: stored values through the position map, vectors renumbered
+    k_gather_src<<<grid_for(ctx->SA.entries), 256, 0, s>>>(ctx->SA.entries, ctx->A_val, ctx->SA.src, ctx->SA.val); CKL();
+    k_gather_src<<<grid_for(ctx->ST.entries), 256, 0, s>>>(ctx->ST.entries, ctx->T_val, ctx->ST.src, ctx->ST.val); CKL();
+    k_permute<<<gm, 256, 0, s>>>(m, ctx->b_s, ctx->perm_r, ctx->bp); CKL();
+    k_permute<<<gm, 256, 0, s>>>(m, ctx->wr, ctx->perm_r, ctx->wrp); CKL();
+    k_permute<<<gn, 256, 0, s>>>(n, ctx->c_s, ctx->perm_c, ctx->cp); CKL();
+    k_permute<<<gn, 256, 0, s>>>(n, ctx->l_s, ctx->perm_c, ctx->lp); CKL();
+    k_permute<<<gn, 256, 0, s>>>(n, ctx->u_s, ctx->perm_c, ctx->up); CKL();
+    k_permute<<<gn, 256, 0, s>>>(n, ctx->wc, ctx->perm_c, ctx->wcp); CKL();
     CK(cudaStreamSynchronize(s));
     return HPR_OK;
 }
@@ -686,6 +879,7 @@ int hpr_create(hpr_ctx **out, const hpr_csr *A1, const hpr_csr *A2, const double
         ctx->err = "this library is built for sm_103 (B300) only";
         return bail(HPR_ERR_NO_DEVICE);
     }
+    ctx->num_sms = prop.multiProcessorCount;
     ctx->m1 = r1;
     ctx->m2 = r2;
     ctx->m = r1 + r2;
@@ -822,34 +1016,9 @@ int hpr_solve(hpr_ctx *ctx, double tol)
             for (int i = 0; i < L; ++i) {
                 const bool last = (i == L - 1);
                 const bool r0 = (i == 0 && first_r0);
-                // every traced iteration runs in check mode so that x_bar, y_bar are stored
-                ctx->launches += 2;
-                if (ctx->ntT) k_phase_x<true><<<ctx->ntT, TB, 0, s>>>(xargs(ctx), i);
-                CKL();
-                if (ctx->ntA) k_phase_y<true><<<ctx->ntA, TB, 0, s>>>(yargs(ctx), i);
-                CKL();
-                if (last || r0) {
-                    // residual passes and reductions of a check iteration
-                    DualArgs d;
-                    d.tiles = ctx->tilesT; d.rp = ctx->T_rp; d.ci = ctx->T_ci; d.val = ctx->T_val;
-                    d.ybar = ctx->ybar; d.c = ctx->c_s; d.zbar = ctx->zbar; d.wc = ctx->wc;
-                    d.partials = ctx->partials; d.pstride = ctx->pstride;
-                    if (ctx->ntT) k_check_dual<<<ctx->ntT, TB, 0, s>>>(d);
-                    CKL();
-                    PrimalArgs p;
-                    p.tiles = ctx->tilesA; p.rp = ctx->A_rp; p.ci = ctx->A_ci; p.val = ctx->A_val;
-                    p.xbar = ctx->xbar; p.dx = ctx->dx; p.b = ctx->b_s; p.wr = ctx->wr; p.dy = ctx->dy;
-                    p.partials = ctx->partials; p.pstride = ctx->pstride; p.m1 = (int)ctx->m1;
-                    if (ctx->ntA) k_check_primal<<<ctx->ntA, TB, 0, s>>>(p);
-                    CKL();
-                    ctx->launches += 2;
-                    const int nT = ctx->ntT, nA = ctx->ntA;
-                    st = launch_reduce(ctx, {{Q_DX2, nT}, {Q_XX0, nT}, {Q_CX, nT}, {Q_BND, nT},
-                                             {Q_DY2, nA}, {Q_YY0, nA}, {Q_BY, nA}, {Q_RD, nT},
-                                             {Q_RP, nA}, {Q_CROSS, nA}},
-                                       ctx->scal + (last ? 1 : 0) * NQ);
-                    if (st) return st;
-                }
+                // every traced iteration stores x_bar, y_bar; checks also reduce
+                st = enqueue_iteration(ctx, i, true, last || r0, last ? 1 : 0);
+                if (st) return st;
                 if (!last) {
                     st = trace_copy(ctx, k + i);
                     if (st) return st;
@@ -983,8 +1152,8 @@ int hpr_solve(hpr_ctx *ctx, double tol)
 
     // output: the last w_bar mapped back to the original LP
     k_backmap<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->beta_b, ctx->beta_c, ctx->xbar,
-                                              ctx->ybar, ctx->zbar, ctx->Dr, ctx->Dc, ctx->l_o,
-                                              ctx->u_o, ctx->xo, ctx->yo, ctx->zo);
+                                              ctx->ybar, ctx->zbar, ctx->perm_c, ctx->perm_r, ctx->Dr,
+                                              ctx->Dc, ctx->l_o, ctx->u_o, ctx->xo, ctx->yo, ctx->zo);
     CKL();
     ctx->launches += 1;
     CK(cudaStreamSynchronize(s));
@@ -1057,12 +1226,18 @@ int hpr_get_trace(const hpr_ctx *cctx, int64_t k, double *xbar, double *xhat, do
     const int64_t n = ctx->n, m = ctx->m;
     const double *rec = ctx->trace + (size_t)k * (size_t)(3 * n + 2 * m);
     cudaStream_t s = ctx->stream;
-    if (xbar) CK(cudaMemcpyAsync(xbar, rec, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    if (xhat) CK(cudaMemcpyAsync(xhat, rec + n, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    if (x) CK(cudaMemcpyAsync(x, rec + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    if (ybar) CK(cudaMemcpyAsync(ybar, rec + 3 * n, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
-    if (y) CK(cudaMemcpyAsync(y, rec + 3 * n + m, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    // the trace holds renumbered vectors: restore the original order on the way out
+    double *outs[5] = {xbar, xhat, x, ybar, y};
+    const int64_t off[5] = {0, n, 2 * n, 3 * n, 3 * n + m};
+    for (int v = 0; v < 5; ++v) {
+        if (!outs[v]) continue;
+        const bool isx = v < 3;
+        const int64_t len = isx ? n : m;
+        k_unpermute<<<grid_for(len), 256, 0, s>>>(len, rec + off[v], isx ? ctx->perm_c : ctx->perm_r, ctx->unperm);
+        CKL();
+        CK(cudaMemcpyAsync(outs[v], ctx->unperm, sizeof(double) * len, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
     return HPR_OK;
 }
 
@@ -1086,9 +1261,9 @@ int hpr_time_iteration(hpr_ctx *ctx, int64_t reps, double *ms_x, double *ms_y, d
     int rc = HPR_OK;
     for (int64_t r = 0; r < reps && rc == HPR_OK; ++r) {
         cudaEventRecord(ev[0], s);
-        if (ctx->ntT) k_phase_x<false><<<ctx->ntT, TB, 0, s>>>(xargs(ctx), 0);
+        if ((rc = launch_sell(ctx, ctx->ST, ctx->grids.X, epi_x<false>(ctx, 0)))) break;
         cudaEventRecord(ev[1], s);
-        if (ctx->ntA) k_phase_y<false><<<ctx->ntA, TB, 0, s>>>(yargs(ctx), 0);
+        if ((rc = launch_sell(ctx, ctx->SA, ctx->grids.Y, epi_y<false>(ctx, 0)))) break;
         cudaEventRecord(ev[2], s);
         cudaError_t e = cudaEventSynchronize(ev[2]);
         if (e != cudaSuccess) { rc = fail_cuda(ctx, e, "hpr_time_iteration", __LINE__); break; }

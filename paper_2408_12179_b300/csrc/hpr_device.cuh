@@ -10,13 +10,12 @@
 //       q = (A xhat)_i;  ybar = y_i + (b_i - q)/(lambda sigma), clamped at 0 for i >= m1
 //       yhat = 2 ybar - y_i;  y_i <- y0_i/(t+2) + (t+1)/(t+2) yhat
 //
-// Both phases are one CSR SpMV each with the elementwise work fused as an epilogue, so
-// every vector crosses HBM once per iteration.  B300 executes FP64 at a small fraction
-// of its FP32 rate, so the SpMV spends exactly one FP64 FMA per nonzero: the nonzeros
-// of a tile are split evenly over the threads (KPT consecutive nonzeros each), every
-// thread accumulates its row fragments with FMA, and fragments of rows that straddle
-// threads are combined afterwards in a fixed order.  All reductions (row sums, CTA
-// partials, final sums) have a fixed order, so results are bitwise reproducible.
+// Both phases are one sparse matrix-vector product each with the elementwise work
+// fused as an epilogue, so every vector crosses HBM once per iteration.  B300 executes
+// FP64 at a small fraction of its FP32 rate, so the products use a sliced-ELL layout in
+// which every FP64 instruction is issued by a full warp of useful lanes (see k_sell).
+// All reductions (row sums, CTA partials, final sums) have a fixed order, so results
+// are bitwise reproducible.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,10 +23,11 @@
 
 namespace hprdev {
 
-constexpr int TB = 256;                 // threads per tile CTA
-constexpr int KPT = 7;                  // nonzeros per thread (odd: conflict-free smem reads)
-constexpr int TILE_NNZ = TB * KPT;      // 1792 nonzeros staged per tile
-constexpr int TILE_ROWS = TB;           // at most one epilogue row per thread
+constexpr int TB = 256;                 // threads per CTA
+#ifndef HPR_SELL_CTAS
+#define HPR_SELL_CTAS 4
+#endif
+constexpr int SELL_CTAS_PER_SM = HPR_SELL_CTAS;  // resident CTAs of the sliced-ELL kernels
 
 // quantities reduced at a check (indices into the partials / scalar arrays)
 enum {
@@ -81,305 +81,320 @@ __device__ __forceinline__ double block_sum(double v, double *scratch /* >= TB/3
     return s;
 }
 
-// ------------------------------------------------------------------ tile SpMV
-template <int NV>
-struct TileSmem {
-    double val[TILE_NNZ];
-    int col[TILE_NNZ];
-    int rp[TILE_ROWS + 1];
-    double sum[NV][TILE_ROWS];
-    double tail[NV][TB];
-    double red[TB / 32];
-};
-
-// Row sums of rows [r0, r1) of a CSR matrix against NV dense vectors, left in
-// sm.sum[v][row - r0].  A tile holds either at most TILE_ROWS rows with at most
-// TILE_NNZ nonzeros in total, or a single longer row.
-template <int NV>
-__device__ __forceinline__ void tile_spmv(const int *__restrict__ rp, const int *__restrict__ ci,
-                                          const double *__restrict__ val,
-                                          const double *__restrict__ xa,
-                                          const double *__restrict__ xb, int r0, int r1,
-                                          TileSmem<NV> &sm)
+// ------------------------------------------------------------------ FP64-free helpers
+// Order-preserving map of a (non-NaN) double onto a signed 64-bit integer, so that the
+// projections compare on the integer pipes (B300's FP64 pipe is the scarce one).
+__device__ __forceinline__ long long dkey(double v)
 {
-    const int tid = threadIdx.x;
-    const int R = r1 - r0;
-    const int p0 = rp[r0];
-    const int N = rp[r1] - p0;
-
-    if (N > TILE_NNZ) {
-        // one long row: strided coalesced FMA accumulation, then a fixed-order tree
-        double acc0 = 0.0, acc1 = 0.0;
-        for (int p = p0 + tid; p < p0 + N; p += TB) {
-            const double a = val[p];
-            const int c = ci[p];
-            acc0 = fma(a, __ldg(xa + c), acc0);
-            if (NV == 2) acc1 = fma(a, __ldg(xb + c), acc1);
-        }
-        double s0 = block_sum(acc0, sm.red);
-        if (tid == 0) sm.sum[0][0] = s0;
-        if (NV == 2) {
-            double s1 = block_sum(acc1, sm.red);
-            if (tid == 0) sm.sum[NV - 1][0] = s1;
-        }
-        __syncthreads();
-        return;
-    }
-
-    // stage the tile's nonzeros and row pointers (coalesced)
-    for (int i = tid; i < N; i += TB) {
-        sm.val[i] = val[p0 + i];
-        sm.col[i] = ci[p0 + i];
-    }
-    for (int i = tid; i <= R; i += TB) sm.rp[i] = rp[r0 + i] - p0;
-    for (int i = tid; i < R; i += TB) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sm.sum[v][i] = 0.0;
-    }
-    __syncthreads();
-
-    const int a = tid * KPT;
-    int head_row = -1;
-    double head[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) head[v] = 0.0;
-
-    if (a < N) {
-        const int b = min(a + KPT, N);
-        // row holding nonzero a: sm.rp[lo] <= a < sm.rp[lo+1]
-        int lo = 0, hi = R;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (sm.rp[mid] <= a) lo = mid;
-            else hi = mid;
-        }
-        int row = lo;
-        int row_start = sm.rp[row];
-        int row_end = sm.rp[row + 1];
-
-        double vv[KPT], g0[KPT], g1[KPT];
-#pragma unroll
-        for (int k = 0; k < KPT; ++k) {
-            const int p = a + k;
-            if (p < b) {
-                const int c = sm.col[p];
-                vv[k] = sm.val[p];
-                g0[k] = __ldg(xa + c);
-                if (NV == 2) g1[k] = __ldg(xb + c);
-            }
-        }
-        double acc[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-#pragma unroll
-        for (int k = 0; k < KPT; ++k) {
-            const int p = a + k;
-            if (p < b) {
-                while (row_end <= p) {
-                    // the current row ends before p: emit its fragment
-                    if (row_start < a) {
-                        head_row = row;
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) head[v] = acc[v];
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) sm.sum[v][row] = acc[v];
-                    }
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-                    ++row;
-                    row_start = row_end;
-                    row_end = sm.rp[row + 1];
-                }
-                acc[0] = fma(vv[k], g0[k], acc[0]);
-                if (NV == 2) acc[NV - 1] = fma(vv[k], g1[k], acc[NV - 1]);
-            }
-        }
-        if (row_end == b) {
-            if (row_start < a) {
-                head_row = row;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) head[v] = acc[v];
-            } else {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) sm.sum[v][row] = acc[v];
-            }
-        } else {
-            // the row continues in the next thread(s)
-#pragma unroll
-            for (int v = 0; v < NV; ++v) sm.tail[v][tid] = acc[v];
-        }
-    }
-    __syncthreads();
-    if (head_row >= 0) {
-        // this thread holds the last fragment of a row that started in thread t0:
-        // sum the fragments in thread order
-        const int t0 = sm.rp[head_row] / KPT;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            double s = sm.tail[v][t0];
-            for (int t = t0 + 1; t < tid; ++t) s += sm.tail[v][t];
-            sm.sum[v][head_row] = s + head[v];
-        }
-    }
-    __syncthreads();
+    const long long i = __double_as_longlong(v);
+    return i ^ ((i >> 63) & 0x7fffffffffffffffLL);
 }
 
-// ------------------------------------------------------------------ HPR phase X
-struct XArgs {
-    const int *tiles, *rp, *ci;   // CSR of A^T (rows = columns of A)
-    const double *val;
-    const double *y;              // gathered
+// min(max(v, l), u) for l <= u (Pi_[l,u]); -0 orders below +0
+__device__ __forceinline__ double clamp_lu(double v, double l, double u)
+{
+    const long long kv = dkey(v);
+    double r = v;
+    if (kv < dkey(l)) r = l;
+    if (kv > dkey(u)) r = u;
+    return r;
+}
+
+// max(v, 0) (Pi_{R_+}) from the sign bit
+__device__ __forceinline__ double pos_part(double v)
+{
+    return __double_as_longlong(v) < 0 ? 0.0 : v;
+}
+
+// ------------------------------------------------------------------ sliced-ELL SpMV
+// B300 issues one FP64 warp instruction every ~17 cycles per SM whatever the number of
+// active lanes, and a dependent DFMA takes ~70 cycles.  So the SpMV keeps all 32 lanes
+// of every FP64 instruction busy with useful work.  Rows are renumbered by decreasing
+// length (stable) and taken in groups of 32.  A group gives each row L = 1, 2, ..., 32
+// lanes (L grows with the group's longest row so that a slice needs at most ~40 steps)
+// and is stored as L slices of 32/L rows, each column-major so that a warp reads 32
+// consecutive values per step (sliced ELL with a global sort; padding entries are
+// zeros).  A lane accumulates every L-th entry of its row with FMA; the L partial sums
+// of a row are added by a fixed xor butterfly and moved to the row's own lane, so the
+// epilogue of the group runs once, on 32 lanes, whatever L is.  The slices are split over
+// the warps of the grid in contiguous runs of about equal cost (host-made table) that
+// keep light groups whole and split heavy ones by slice; consecutive runs go to
+// different CTAs.
+struct SellArgs {
+    int rows;             // rows of the matrix (in the renumbered order)
+    int nslices;
+    const int *srow;      // nslices + 1: first row of each slice
+    const int *sptr;      // nslices + 1: first stored entry; slice s has (sptr[s+1]-sptr[s])/32 steps
+    const unsigned char *slg;   // log2 of the lanes per row of each slice
+    const int *wstart;    // runs + 1: run i covers slices [wstart[i], wstart[i+1])
+    const double *val;    // stored values (padding: 0)
+    const int *col;       // stored column indices (padding: 0)
+    const int *skip;      // optional: the kernel does nothing while *skip != 0
+};
+
+// E supplies NV gathered vectors xa (, xb), NP partial sums (ids q[]), a Pre record of
+// epilogue operands (prefetch(j)) and row(j, act, s, pre, part).
+template <class E>
+__global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
+{
+    constexpr int NV = E::NV, NP = E::NP;
+    __shared__ double red[TB / 32];
+    if (S.skip && *S.skip) return;
+    E ee = e;
+    ee.load();
+    const int lane = threadIdx.x & 31;
+    const int run = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // spreads runs over CTAs
+    double part[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int i = 0; i < (NP > 0 ? NP : 1); ++i) part[i] = 0.0;
+
+    int buf_r0 = 0, buf_n = 0;                   // rows [buf_r0, buf_r0 + buf_n) hold sums
+    double buf0 = 0.0, buf1 = 0.0;               // lane t: sum of row buf_r0 + t
+    typename E::Pre pre{};
+    const int s_end = S.wstart[run + 1];
+    for (int s = S.wstart[run]; s < s_end; ++s) {
+        const int lg = S.slg[s];
+        const int r0 = S.srow[s], nrows = S.srow[s + 1] - r0;
+        const int base = S.sptr[s];
+        const int steps = (S.sptr[s + 1] - base) >> 5;
+        if (buf_n + nrows > 32) {                 // run started inside a group: flush early
+            const int j = min(buf_r0 + lane, S.rows - 1);
+            const double sums[2] = {buf0, buf1};
+            ee.row(j, lane < buf_n, sums, pre, part);
+            buf_n = 0;
+        }
+        if (buf_n == 0) {
+            buf_r0 = r0;                          // operands of the next 32 rows, early
+            pre = ee.prefetch(min(r0 + lane, S.rows - 1));
+        }
+        const double *pv = S.val + base + lane;
+        const int *pc = S.col + base + lane;
+        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+        int k = 0;
+        for (; k + 4 <= steps; k += 4) {
+            double v[4], g0[4], g1[4];
+            int c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v[u] = __ldcs(pv + (k + u) * 32);
+                c[u] = __ldcs(pc + (k + u) * 32);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                g0[u] = __ldg(ee.xa + c[u]);
+                if (NV == 2) g1[u] = __ldg(ee.xb + c[u]);
+            }
+            // two chains (even / odd steps) halve the dependent FMA latency
+            a0 = fma(v[0], g0[0], a0);
+            a1 = fma(v[1], g0[1], a1);
+            a0 = fma(v[2], g0[2], a0);
+            a1 = fma(v[3], g0[3], a1);
+            if (NV == 2) {
+                b0 = fma(v[0], g1[0], b0);
+                b1 = fma(v[1], g1[1], b1);
+                b0 = fma(v[2], g1[2], b0);
+                b1 = fma(v[3], g1[3], b1);
+            }
+        }
+        for (; k < steps; ++k) {
+            const double v = __ldcs(pv + k * 32);
+            const int c = __ldcs(pc + k * 32);
+            a0 = fma(v, __ldg(ee.xa + c), a0);
+            if (NV == 2) b0 = fma(v, __ldg(ee.xb + c), b0);
+        }
+        if (steps >= 4) {                         // warp-uniform
+            a0 += a1;
+            if (NV == 2) b0 += b1;
+        }
+        for (int o = 1; o < (1 << lg); o <<= 1) { // warp-uniform: lg is per slice
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            if (NV == 2) b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+        }
+        // row q of this slice (held by lanes q*L ...) moves to lane buf_n + q
+        const int src = (int)(((unsigned)(lane - buf_n) << lg) & 31u);
+        const double m0 = __shfl_sync(0xffffffffu, a0, src);
+        const double m1 = NV == 2 ? __shfl_sync(0xffffffffu, b0, src) : 0.0;
+        if (lane >= buf_n && lane < buf_n + nrows) {
+            buf0 = m0;
+            buf1 = m1;
+        }
+        buf_n += nrows;
+        if (buf_n == 32 || s + 1 == s_end) {      // a full group (or the end of the run)
+            const int j = min(buf_r0 + lane, S.rows - 1);
+            const double sums[2] = {buf0, buf1};
+            ee.row(j, lane < buf_n, sums, pre, part);
+            buf_n = 0;
+        }
+    }
+
+    if (NP > 0) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const double t = block_sum(part[i], red);
+            if (threadIdx.x == 0) ee.partials[ee.q[i] * ee.pstride + blockIdx.x] = t;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ epilogues
+// phase X (rows of A^T = columns j of A): eq. (update-x), reflection, Halpern step;
+// check mode also stores x_bar, z_bar (eq. update-z), x - x_bar and the partial sums
+template <bool CHECK>
+struct EpiX {
+    static constexpr int NV = 1, NP = CHECK ? 4 : 0;
+    const double *xa, *xb;       // gathered: y
+    int q[4];
+    double *partials;
+    int pstride;
     const double *c, *l, *u, *x0;
-    double *x, *xhat;
-    double *xbar, *zbar, *dx;     // check mode only
-    double *partials;
-    int pstride;
-    const DevCtl *ctl;
-};
-
-template <bool CHECK>
-__global__ void __launch_bounds__(TB) k_phase_x(XArgs A, int it)
-{
-    __shared__ TileSmem<1> sm;
-    const int r0 = A.tiles[blockIdx.x], r1 = A.tiles[blockIdx.x + 1];
-    tile_spmv<1>(A.rp, A.ci, A.val, A.y, nullptr, r0, r1, sm);
-    const double sigma = A.ctl->sigma;
-    const double ha = A.ctl->h[2 * it], hb = A.ctl->h[2 * it + 1];
-    double p_dx = 0.0, p_xx0 = 0.0, p_cx = 0.0, p_bnd = 0.0;
-    for (int i = threadIdx.x; i < r1 - r0; i += TB) {
-        const int j = r0 + i;
-        const double xj = A.x[j];
-        const double cj = A.c[j], lj = A.l[j], uj = A.u[j], x0j = A.x0[j];
-        const double v = fma(sigma, sm.sum[0][i] - cj, xj);   // x + sigma (A^T y - c)
-        const double xb = fmin(fmax(v, lj), uj);               // Pi_C, eq. (update-x)
-        const double xh = 2.0 * xb - xj;                       // reflection
-        A.xhat[j] = xh;
-        A.x[j] = fma(hb, xh, ha * x0j);                        // Halpern step
-        if (CHECK) {
-            const double zb = (xb - v) / sigma;                // eq. (update-z)
-            const double d = xj - xb;
-            A.xbar[j] = xb;
-            A.zbar[j] = zb;
-            A.dx[j] = d;
-            p_dx = fma(d, d, p_dx);
-            p_xx0 = fma(xb - x0j, xb - x0j, p_xx0);
-            p_cx = fma(cj, xb, p_cx);
-            if (zb > 0.0) p_bnd = fma(zb, lj, p_bnd);
-            else if (zb < 0.0) p_bnd = fma(zb, uj, p_bnd);
+    double *x, *xhat, *xbar, *zbar, *dx;
+    const DevCtl *ctl;           // sigma and the Halpern weights of iteration `it`
+    int it;
+    double sigma, ha, hb;
+    struct Pre { double x, x0, c, l, u; };
+    __device__ __forceinline__ void load()
+    {
+        sigma = ctl->sigma;
+        ha = ctl->h[2 * it];
+        hb = ctl->h[2 * it + 1];
+    }
+    __device__ __forceinline__ Pre prefetch(int j) const
+    {
+        return Pre{x[j], x0[j], c[j], l[j], u[j]};
+    }
+    __device__ __forceinline__ void row(int j, bool act, const double *s, const Pre &p,
+                                        double *part) const
+    {
+        const double v = fma(sigma, s[0] - p.c, p.x);   // x + sigma (A^T y - c)
+        const double xb_ = clamp_lu(v, p.l, p.u);       // Pi_C
+        const double xh = fma(2.0, xb_, -p.x);          // 2 x_bar - x
+        const double xn = fma(hb, xh, ha * p.x0);       // x0/(t+2) + (t+1)/(t+2) x_hat
+        if (act) {
+            xhat[j] = xh;
+            x[j] = xn;
+        }
+        if (CHECK && act) {
+            const double zb = (xb_ - v) / sigma;
+            const double d = p.x - xb_;
+            xbar[j] = xb_;
+            zbar[j] = zb;
+            dx[j] = d;
+            part[0] = fma(d, d, part[0]);
+            part[1] = fma(xb_ - p.x0, xb_ - p.x0, part[1]);
+            part[2] = fma(p.c, xb_, part[2]);
+            if (zb > 0.0) part[3] = fma(zb, p.l, part[3]);
+            else if (zb < 0.0) part[3] = fma(zb, p.u, part[3]);
         }
     }
-    if (CHECK) {
-        double s;
-        s = block_sum(p_dx, sm.red);  if (threadIdx.x == 0) A.partials[Q_DX2 * A.pstride + blockIdx.x] = s;
-        s = block_sum(p_xx0, sm.red); if (threadIdx.x == 0) A.partials[Q_XX0 * A.pstride + blockIdx.x] = s;
-        s = block_sum(p_cx, sm.red);  if (threadIdx.x == 0) A.partials[Q_CX * A.pstride + blockIdx.x] = s;
-        s = block_sum(p_bnd, sm.red); if (threadIdx.x == 0) A.partials[Q_BND * A.pstride + blockIdx.x] = s;
-    }
-}
+};
 
-// ------------------------------------------------------------------ HPR phase Y
-struct YArgs {
-    const int *tiles, *rp, *ci;   // CSR of A
-    const double *val;
-    const double *xhat;           // gathered
+// phase Y (rows i of A): eq. (update-y-2), reflection, Halpern step; check mode also
+// stores y_bar, y - y_bar and the partial sums
+template <bool CHECK>
+struct EpiY {
+    static constexpr int NV = 1, NP = CHECK ? 3 : 0;
+    const double *xa, *xb;       // gathered: x_hat
+    int q[3];
+    double *partials;
+    int pstride;
     const double *b, *y0;
-    double *y;
-    double *ybar, *dy;            // check mode only
-    double *partials;
-    int pstride;
-    int m1;
-    const DevCtl *ctl;
-};
-
-template <bool CHECK>
-__global__ void __launch_bounds__(TB) k_phase_y(YArgs A, int it)
-{
-    __shared__ TileSmem<1> sm;
-    const int r0 = A.tiles[blockIdx.x], r1 = A.tiles[blockIdx.x + 1];
-    tile_spmv<1>(A.rp, A.ci, A.val, A.xhat, nullptr, r0, r1, sm);
-    const double inv_ls = A.ctl->inv_ls;
-    const double ha = A.ctl->h[2 * it], hb = A.ctl->h[2 * it + 1];
-    double p_dy = 0.0, p_yy0 = 0.0, p_by = 0.0;
-    for (int ii = threadIdx.x; ii < r1 - r0; ii += TB) {
-        const int i = r0 + ii;
-        const double yi = A.y[i], bi = A.b[i], y0i = A.y0[i];
-        double yb = fma(bi - sm.sum[0][ii], inv_ls, yi);       // eq. (update-y-2)
-        if (i >= A.m1) yb = fmax(yb, 0.0);                     // Pi_{R^m2_+}
-        const double yh = 2.0 * yb - yi;                       // reflection
-        A.y[i] = fma(hb, yh, ha * y0i);                        // Halpern step
-        if (CHECK) {
-            const double d = yi - yb;
-            A.ybar[i] = yb;
-            A.dy[i] = d;
-            p_dy = fma(d, d, p_dy);
-            p_yy0 = fma(yb - y0i, yb - y0i, p_yy0);
-            p_by = fma(bi, yb, p_by);
+    double *y, *ybar, *dy;
+    const DevCtl *ctl;           // 1/(lambda sigma) and the Halpern weights of iteration `it`
+    int it;
+    const unsigned char *ineq;   // ineq[i] = 1 for the rows of A2 (renumbered order)
+    double inv_ls, ha, hb;
+    struct Pre { double y, b, y0; unsigned char ineq; };
+    __device__ __forceinline__ void load()
+    {
+        inv_ls = ctl->inv_ls;
+        ha = ctl->h[2 * it];
+        hb = ctl->h[2 * it + 1];
+    }
+    __device__ __forceinline__ Pre prefetch(int i) const
+    {
+        return Pre{y[i], b[i], y0[i], ineq[i]};
+    }
+    __device__ __forceinline__ void row(int i, bool act, const double *s, const Pre &p,
+                                        double *part) const
+    {
+        double yb = fma(p.b - s[0], inv_ls, p.y);       // y + (b - A x_hat) / (lambda sigma)
+        if (p.ineq) yb = pos_part(yb);                  // Pi_{R^m2_+}
+        const double yh = fma(2.0, yb, -p.y);
+        const double yn = fma(hb, yh, ha * p.y0);
+        if (act) y[i] = yn;
+        if (CHECK && act) {
+            const double d = p.y - yb;
+            ybar[i] = yb;
+            dy[i] = d;
+            part[0] = fma(d, d, part[0]);
+            part[1] = fma(yb - p.y0, yb - p.y0, part[1]);
+            part[2] = fma(p.b, yb, part[2]);
         }
     }
-    if (CHECK) {
-        double s;
-        s = block_sum(p_dy, sm.red);  if (threadIdx.x == 0) A.partials[Q_DY2 * A.pstride + blockIdx.x] = s;
-        s = block_sum(p_yy0, sm.red); if (threadIdx.x == 0) A.partials[Q_YY0 * A.pstride + blockIdx.x] = s;
-        s = block_sum(p_by, sm.red);  if (threadIdx.x == 0) A.partials[Q_BY * A.pstride + blockIdx.x] = s;
-    }
-}
-
-// ------------------------------------------------------------------ check passes
-// dual residual (Section 4.1) in original-space weights w_c = beta_c / D_c
-struct DualArgs {
-    const int *tiles, *rp, *ci;
-    const double *val;
-    const double *ybar, *c, *zbar, *wc;
-    double *partials;
-    int pstride;
 };
 
-__global__ void __launch_bounds__(TB) k_check_dual(DualArgs A)
-{
-    __shared__ TileSmem<1> sm;
-    const int r0 = A.tiles[blockIdx.x], r1 = A.tiles[blockIdx.x + 1];
-    tile_spmv<1>(A.rp, A.ci, A.val, A.ybar, nullptr, r0, r1, sm);
-    double p = 0.0;
-    for (int i = threadIdx.x; i < r1 - r0; i += TB) {
-        const int j = r0 + i;
-        const double r = A.wc[j] * (A.c[j] - sm.sum[0][i] - A.zbar[j]);
-        p = fma(r, r, p);
-    }
-    const double s = block_sum(p, sm.red);
-    if (threadIdx.x == 0) A.partials[Q_RD * A.pstride + blockIdx.x] = s;
-}
-
-// primal residual with weights w_r = beta_b / D_r, and the cross term <dy, A dx> of
-// the M-norm (eq. def:M with T1 = lambda I - A A^*)
-struct PrimalArgs {
-    const int *tiles, *rp, *ci;
-    const double *val;
-    const double *xbar, *dx, *b, *wr, *dy;
+// dual residual of Section 4.1 in original-space weights w_c = beta_c / D_c
+struct EpiDual {
+    static constexpr int NV = 1, NP = 1;
+    const double *xa, *xb;       // gathered: y_bar
+    int q[1];
     double *partials;
     int pstride;
-    int m1;
+    const double *c, *zbar, *wc;
+    struct Pre { double c, z, w; };
+    __device__ __forceinline__ void load() {}
+    __device__ __forceinline__ Pre prefetch(int j) const { return Pre{c[j], zbar[j], wc[j]}; }
+    __device__ __forceinline__ void row(int, bool act, const double *s, const Pre &p, double *part) const
+    {
+        const double r = p.w * (p.c - s[0] - p.z);
+        if (act) part[0] = fma(r, r, part[0]);
+    }
 };
 
-__global__ void __launch_bounds__(TB) k_check_primal(PrimalArgs A)
-{
-    __shared__ TileSmem<2> sm;
-    const int r0 = A.tiles[blockIdx.x], r1 = A.tiles[blockIdx.x + 1];
-    tile_spmv<2>(A.rp, A.ci, A.val, A.xbar, A.dx, r0, r1, sm);
-    double pr = 0.0, pc = 0.0;
-    for (int ii = threadIdx.x; ii < r1 - r0; ii += TB) {
-        const int i = r0 + ii;
-        double r = A.b[i] - sm.sum[0][ii];
-        if (i >= A.m1) r = fmax(r, 0.0);                       // Pi_D
-        r *= A.wr[i];
-        pr = fma(r, r, pr);
-        pc = fma(A.dy[i], sm.sum[1][ii], pc);
+// primal residual with weights w_r = beta_b / D_r and the cross term <dy, A dx> of the
+// M-norm (eq. def:M with T1 = lambda I - A A^*)
+struct EpiPrimal {
+    static constexpr int NV = 2, NP = 2;
+    const double *xa, *xb;       // gathered: x_bar, x - x_bar
+    int q[2];
+    double *partials;
+    int pstride;
+    const double *b, *wr, *dy;
+    const unsigned char *ineq;
+    struct Pre { double b, w, dy; unsigned char ineq; };
+    __device__ __forceinline__ void load() {}
+    __device__ __forceinline__ Pre prefetch(int i) const { return Pre{b[i], wr[i], dy[i], ineq[i]}; }
+    __device__ __forceinline__ void row(int, bool act, const double *s, const Pre &p, double *part) const
+    {
+        double r = p.b - s[0];
+        if (p.ineq) r = pos_part(r);                    // Pi_D
+        r *= p.w;
+        if (act) {
+            part[0] = fma(r, r, part[0]);
+            part[1] = fma(p.dy, s[1], part[1]);
+        }
     }
-    double s = block_sum(pr, sm.red);
-    if (threadIdx.x == 0) A.partials[Q_RP * A.pstride + blockIdx.x] = s;
-    s = block_sum(pc, sm.red);
-    if (threadIdx.x == 0) A.partials[Q_CROSS * A.pstride + blockIdx.x] = s;
-}
+};
+
+// power method: out = M xin and the partial ||out||^2
+struct EpiNorm {
+    static constexpr int NV = 1, NP = 1;
+    const double *xa, *xb;
+    int q[1];
+    double *partials;
+    int pstride;
+    double *out;
+    struct Pre { int unused; };
+    __device__ __forceinline__ void load() {}
+    __device__ __forceinline__ Pre prefetch(int) const { return Pre{0}; }
+    __device__ __forceinline__ void row(int j, bool act, const double *s, const Pre &, double *part) const
+    {
+        if (act) {
+            out[j] = s[0];
+            part[0] = fma(s[0], s[0], part[0]);
+        }
+    }
+};
 
 // ------------------------------------------------------------------ final reduction
 struct RedSpec {
@@ -420,20 +435,48 @@ __global__ void k_restart(int n, int m, const double *__restrict__ xbar,
     }
 }
 
-// back-map of w_bar to the original LP: x = Pi_C(beta_b D_c xbar), y = beta_c D_r ybar,
-// z = beta_c zbar / D_c
+// back-map of w_bar (renumbered) to the original LP in its original order:
+// x = Pi_C(beta_b D_c xbar), y = beta_c D_r ybar, z = beta_c zbar / D_c
 __global__ void k_backmap(int n, int m, double beta_b, double beta_c, const double *xbar,
-                          const double *ybar, const double *zbar, const double *Dr,
-                          const double *Dc, const double *lo, const double *uo, double *xo,
-                          double *yo, double *zo)
+                          const double *ybar, const double *zbar, const int *perm_c,
+                          const int *perm_r, const double *Dr, const double *Dc,
+                          const double *lo, const double *uo, double *xo, double *yo, double *zo)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
         if (i < n) {
-            xo[i] = fmin(fmax(beta_b * Dc[i] * xbar[i], lo[i]), uo[i]);
-            zo[i] = beta_c * zbar[i] / Dc[i];
+            const int o = perm_c[i];
+            xo[o] = fmin(fmax(beta_b * Dc[o] * xbar[i], lo[o]), uo[o]);
+            zo[o] = beta_c * zbar[i] / Dc[o];
         } else {
-            yo[i - n] = beta_c * Dr[i - n] * ybar[i - n];
+            const int o = perm_r[i - n];
+            yo[o] = beta_c * Dr[o] * ybar[i - n];
         }
+    }
+}
+
+// dst[i] = src[perm[i]] (into the renumbered order)
+__global__ void k_permute(int64_t len, const double *__restrict__ src, const int *__restrict__ perm,
+                          double *dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[perm[i]];
+}
+
+// dst[perm[i]] = src[i] (back to the original order)
+__global__ void k_unpermute(int64_t len, const double *__restrict__ src, const int *__restrict__ perm,
+                            double *dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        dst[perm[i]] = src[i];
+}
+
+// stored values of a sliced-ELL matrix from the CSR values (-1: padding, value 0)
+__global__ void k_gather_src(int64_t len, const double *__restrict__ csr, const int *__restrict__ src,
+                             double *dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        const int p = src[i];
+        dst[i] = p >= 0 ? csr[p] : 0.0;
     }
 }
 
@@ -447,47 +490,22 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i)
     return z ^ (z >> 31);
 }
 
-// u_i = 2 U_i - 1 and the partial ||u||^2 (one partial per CTA)
-__global__ void __launch_bounds__(TB) k_pow_start(int m, uint64_t seed, double *u,
+// u_i = 2 U_{perm[i]} - 1 (the generator is indexed by the original row) and the
+// partial ||u||^2 (one partial per CTA)
+__global__ void __launch_bounds__(TB) k_pow_start(int m, uint64_t seed, const int *perm, double *u,
                                                   double *partials, int pstride)
 {
     __shared__ double red[TB / 32];
     double p = 0.0;
     const int i = blockIdx.x * TB + threadIdx.x;
     if (i < m) {
-        const double v = 2.0 * ((double)(splitmix64_at(seed, (uint64_t)i) >> 11) * 0x1.0p-53) - 1.0;
+        const uint64_t o = (uint64_t)(perm ? perm[i] : i);
+        const double v = 2.0 * ((double)(splitmix64_at(seed, o) >> 11) * 0x1.0p-53) - 1.0;
         u[i] = v;
         p = v * v;
     }
     const double s = block_sum(p, red);
     if (threadIdx.x == 0) partials[Q_V2 * pstride + blockIdx.x] = s;
-}
-
-struct SpmvNormArgs {
-    const int *tiles, *rp, *ci;
-    const double *val;
-    const double *xin;
-    double *out;
-    double *partials;
-    int pstride, q;
-    const PowCtl *pc;   // skip when pc->done (may be NULL)
-};
-
-// out = M xin over the tile rows and the partial ||out||^2
-__global__ void __launch_bounds__(TB) k_spmv_norm(SpmvNormArgs A)
-{
-    __shared__ TileSmem<1> sm;
-    if (A.pc && A.pc->done) return;
-    const int r0 = A.tiles[blockIdx.x], r1 = A.tiles[blockIdx.x + 1];
-    tile_spmv<1>(A.rp, A.ci, A.val, A.xin, nullptr, r0, r1, sm);
-    double p = 0.0;
-    for (int i = threadIdx.x; i < r1 - r0; i += TB) {
-        const double v = sm.sum[0][i];
-        A.out[r0 + i] = v;
-        p = fma(v, v, p);
-    }
-    const double s = block_sum(p, sm.red);
-    if (threadIdx.x == 0) A.partials[A.q * A.pstride + blockIdx.x] = s;
 }
 
 // after s = A^T u: lambda_k = ||s||^2; stop when |lambda_k - lambda_{k-1}| <= tol lambda_k
