@@ -31,9 +31,9 @@ METRIC = ("time-to-KKT≤1e-8 (s), HPR iters/s, HBM GB/s % of peak; chosen form 
 # DRAM bytes per launch from one ncu capture of the full-size workload (see
 # profiles/), valid only for the kernel source they were taken on.
 NCU_TRAFFIC = {
-    "source_sha1": None,
-    "k_phase_x": None,
-    "k_phase_y": None,
+    "source_sha1": "d230f33a17e04b49215559660b92ba085a572803",
+    "k_phase_x": 88218623,
+    "k_phase_y": 72952576,
 }
 
 
@@ -173,6 +173,8 @@ def run_ours(args):
     lp = workload(args)
     stream = torch.cuda.Stream()
     opts = dict(tol=args.tol, max_iter=args.max_iter, cuda_stream=stream.cuda_stream)
+    if args.lambda_fixed > 0:
+        opts["lambda_fixed"] = args.lambda_fixed   # profiling aid: skips the power method
     solver = hpr.Solver(lp, **opts)
 
     def barrier():
@@ -291,6 +293,8 @@ def main():
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=1)
     ap.add_argument("--sample-iters", dest="sample_iters", type=int, default=150)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    ap.add_argument("--lambda-fixed", dest="lambda_fixed", type=float, default=0.0,
+                    help="use this lambda instead of the power method (short profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
