@@ -112,6 +112,36 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(torch, dist, secs, iters, device):
+    """Whole-job figures over the ranks (replicas): the slowest rank's time and the sum
+    of all ranks' iterations.  dist None: a single process."""
+    if dist is None:
+        return float(secs), float(iters)
+    t = torch.tensor([float(secs)], dtype=torch.float64, device=device)
+    k = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(k, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(k.item())
+
+
+def read_bandwidth_probe(torch):
+    """Read-only HBM bandwidth of this GPU, measured live: a reduction over a 1 GiB FP64
+    tensor (reads 1 GiB, writes nothing), best of 5 with CUDA events.  Context for the
+    roofline: the iteration reads ~16x more bytes than it writes, and on this part a
+    read-only stream tops out well below the copy (read + write) figure used as peak."""
+    t = torch.ones(1 << 27, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 1e30
+    for _ in range(6):
+        e0.record()
+        t.sum()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del t
+    return (1 << 30) / (best * 1e-3) / 1e9
+
+
 def workload(args):
     from paper_2408_12179_b300 import lpgen
 
@@ -197,17 +227,12 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     iters = sum(i["iters"] for i in infos)
-    t = torch.tensor([ms / 1e3, float(iters)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        t[0] = tmax[0]
-    secs, all_iters = float(t[0]), float(t[1])
+    secs, all_iters = aggregate(torch, dist if world > 1 else None, ms / 1e3, iters, "cuda")
     value = all_iters / secs
 
     # live per-kernel timing (CUDA events on the solver's stream) for the roofline
     ms_x, ms_y, ms_it = solver.time_iteration(50)
+    read_ceiling = read_bandwidth_probe(torch)
     bx, by = algorithmic_bytes(lp.nnz, lp.n, lp.m)
     peak, peak_kind = measured_peak()
     dom, dom_ms, dom_bytes = ("k_phase_x", ms_x, bx) if ms_x >= ms_y else ("k_phase_y", ms_y, by)
@@ -268,7 +293,9 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_kind, "bytes_per_launch": dom_bytes,
-                     "ms_per_launch": dom_ms, "ms_phase_x": ms_x, "ms_phase_y": ms_y},
+                     "ms_per_launch": dom_ms, "ms_phase_x": ms_x, "ms_phase_y": ms_y,
+                     "read_only_ceiling_gbs": read_ceiling,
+                     "frac_of_read_only_ceiling": achieved / read_ceiling},
         "gpu_launches": int(sum(i["launches"] for i in infos)),
         "e2e": e2e,
         "clocks": clocks,
