@@ -51,11 +51,15 @@ def measured_peak():
         return 6400.0, "fallback"
 
 
-def algorithmic_bytes(nnz, n, m):
-    """Each array once per launch, gathered vectors counted once, 32-bit indices:
-    x phase: A^T values+indices 12 nnz, row pointers 4n, gather y 8m, read x, x0, c,
-    l, u 40n, write x_hat, x 16n; y phase: 12 nnz, 4m, gather x_hat 8n, read y, y0, b
-    24m, write y 8m."""
+def algorithmic_bytes(nnz, n, m, precision=0):
+    """Each array once per launch, gathered vectors counted once, 32-bit indices.
+    FP64: x phase: A^T values+indices 12 nnz, row pointers 4n, gather y 8m, read x, x0,
+    c, l, u 40n, write x_hat, x 16n; y phase: 12 nnz, 4m, gather x_hat 8n, read y, y0, b
+    24m, write y 8m.  FP32 form: values 4 B, iterates x, x_hat, y 4 B (anchors and data
+    stay FP64): x phase 8 nnz + 4n + 4m + (4 + 8 + 24)n + 8n, y phase 8 nnz + 4m + 4n +
+    (4 + 8 + 8)m + 4m."""
+    if precision == 1:
+        return 8 * nnz + 4 * n + 4 * m + 36 * n + 8 * n, 8 * nnz + 4 * m + 4 * n + 20 * m + 4 * m
     bx = 12 * nnz + 4 * n + 8 * m + 40 * n + 16 * n
     by = 12 * nnz + 4 * m + 8 * n + 24 * m + 8 * m
     return bx, by
@@ -151,7 +155,8 @@ def workload(args):
 def config_dict(args, lp):
     return {"workload": f"medium sparse planted LP (m={lp.m}, m1={lp.m1}, n={lp.n}, nnz={lp.nnz}, "
                         f"Zipf(1.5) column counts, values +-10^U(-3,3), 20% free columns, seed {args.seed})",
-            "scale": args.scale, "tol": args.tol, "precision": "fp64",
+            "scale": args.scale, "tol": args.tol,
+            "precision": "fp64" if args.precision == 0 else "fp32 form, fp64 below kkt 1e-5",
             "l2": "working set per iteration larger than L2 (no flush)"}
 
 
@@ -202,7 +207,8 @@ def run_ours(args):
     hpr.load()
     lp = workload(args)
     stream = torch.cuda.Stream()
-    opts = dict(tol=args.tol, max_iter=args.max_iter, cuda_stream=stream.cuda_stream)
+    opts = dict(tol=args.tol, max_iter=args.max_iter, cuda_stream=stream.cuda_stream,
+                precision=args.precision)
     if args.lambda_fixed > 0:
         opts["lambda_fixed"] = args.lambda_fixed   # profiling aid: skips the power method
     solver = hpr.Solver(lp, **opts)
@@ -233,7 +239,7 @@ def run_ours(args):
     # live per-kernel timing (CUDA events on the solver's stream) for the roofline
     ms_x, ms_y, ms_it = solver.time_iteration(50)
     read_ceiling = read_bandwidth_probe(torch)
-    bx, by = algorithmic_bytes(lp.nnz, lp.n, lp.m)
+    bx, by = algorithmic_bytes(lp.nnz, lp.n, lp.m, args.precision)
     peak, peak_kind = measured_peak()
     dom, dom_ms, dom_bytes = ("k_phase_x", ms_x, bx) if ms_x >= ms_y else ("k_phase_y", ms_y, by)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
@@ -241,6 +247,17 @@ def run_ours(args):
     if NCU_TRAFFIC["source_sha1"] == kernel_source_sha1():
         traffic = NCU_TRAFFIC.get(dom)
     iter_gbs = (bx + by) / (ms_it * 1e-3) / 1e9
+    plain = None
+    if args.compare_fp64 and args.precision != 0:
+        solver.set_options(precision=0)
+        p_ev0, p_ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p_ev0.record(stream)
+        pinfo = solver.solve(args.tol)["info"]
+        p_ev1.record(stream)
+        torch.cuda.synchronize()
+        plain = {"time_to_kkt_1e-8_s": p_ev0.elapsed_time(p_ev1) / 1e3, "iters": pinfo["iters"],
+                 "status": hpr.hpr_status_str(int(pinfo["status"])), "final_kkt": pinfo["kkt"]}
+        solver.set_options(precision=args.precision)
     solver.close()
 
     # end to end through the C ABI with host buffers (upload, preprocessing, solve, download)
@@ -281,12 +298,13 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(args, lp),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
+        "data": "synthetic", "config": config_dict(args, lp),
         "time_to_kkt_1e-8_s": statistics.mean(t8), "time_to_kkt_1e-4_s": statistics.mean(t4),
         "iters_to_kkt_1e-8": infos[-1]["iters"], "iters_to_kkt_1e-4": infos[-1]["iters_to_1e4"],
         "status": hpr.hpr_status_str(int(infos[-1]["status"])), "final_kkt": infos[-1]["kkt"],
         "restarts": infos[-1]["restarts"], "power_iters": infos[-1]["power_iters"],
+        "iters_fp32": infos[-1]["iters_fp32"],
         "effective_hbm_gbs": value * (bx + by) / 1e9,
         "effective_hbm_frac": value * (bx + by) / 1e9 / peak,
         "iteration_kernels_gbs": iter_gbs,
@@ -302,6 +320,8 @@ def run_ours(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if plain is not None:
+        line["plain_fp64"] = plain
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -320,6 +340,10 @@ def main():
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=1)
     ap.add_argument("--sample-iters", dest="sample_iters", type=int, default=150)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="0: FP64; 1: FP32 form, then FP64 below KKT 1e-5")
+    ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true",
+                    help="also time one plain FP64 solve and report it beside the chosen form")
     ap.add_argument("--lambda-fixed", dest="lambda_fixed", type=float, default=0.0,
                     help="use this lambda instead of the power method (short profiling runs)")
     args = ap.parse_args()

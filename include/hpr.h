@@ -83,6 +83,13 @@ typedef struct {
     int64_t verbose;          /* 1: print one line per check to stderr */
     void *cuda_stream;        /* cudaStream_t to order the work after; NULL: the
                                  context's own stream */
+    int64_t precision;        /* 0: FP64 throughout (default).  1: FP32 form first -- FP32
+                                 matrix values and FP32 iterates x, x_hat, y, row sums of
+                                 FP32 products accumulated in double-float, FP64 anchors,
+                                 data, epilogue arithmetic, checks and power method --
+                                 then FP64 iterates from the first check with
+                                 kkt < switch_tol */
+    double switch_tol;        /* KKT level of the switch to FP64 iterates (1e-5) */
 } hpr_options;
 
 /* Result summary (original, unscaled problem). */
@@ -98,6 +105,7 @@ typedef struct {
     int64_t iters, restarts, power_iters, n_checks;
     int64_t launches;             /* kernels launched by the solve (graph nodes included) */
     int64_t status;               /* HPR_OK, HPR_MAX_ITER or HPR_TIME_LIMIT */
+    int64_t iters_fp32;           /* iterations run in the FP32 form (precision 1) */
 } hpr_info;
 
 /* One evaluation of the restart / termination quantities.  kind: 1 = periodic check,
@@ -156,7 +164,8 @@ int hpr_get_trace(const hpr_ctx *ctx, int64_t k, double *xbar, double *xhat, dou
                   double *ybar, double *y);
 
 /* Times `reps` plain HPR iterations (Section 3.3: the A^T phase with the x update,
- * then the A phase with the y update) launched one kernel at a time, with CUDA events
+ * then the A phase with the y update) of the form selected by opt.precision, launched
+ * one kernel at a time, with CUDA events
  * around each kernel on the context's stream.  Starts from the current iterate and
  * advances it (call after hpr_solve).  Writes the average duration in milliseconds of
  * the x phase (ms_x), the y phase (ms_y) and of a whole iteration (ms_iter); any

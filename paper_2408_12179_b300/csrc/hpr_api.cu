@@ -37,7 +37,13 @@ namespace {
 struct GraphKey {
     int L;
     int first;
-    bool operator<(const GraphKey &o) const { return L != o.L ? L < o.L : first < o.first; }
+    int form;      // 0: FP64, 1: FP32 form
+    bool operator<(const GraphKey &o) const
+    {
+        if (L != o.L) return L < o.L;
+        if (first != o.first) return first < o.first;
+        return form < o.form;
+    }
 };
 
 }  // namespace
@@ -53,6 +59,7 @@ struct SellDev {
     int *srow = nullptr, *sptr = nullptr, *wstart = nullptr, *col = nullptr;
     unsigned char *slg = nullptr;
     double *val = nullptr;
+    float *val32 = nullptr;       // FP32 copy of val (the FP32 form)
     int *src = nullptr;           // CSR position of each stored entry (-1: padding)
 };
 
@@ -87,6 +94,8 @@ struct hpr_ctx {
     double *x = nullptr, *x0 = nullptr, *xhat = nullptr, *xbar = nullptr, *zbar = nullptr,
            *dx = nullptr;
     double *y = nullptr, *y0 = nullptr, *ybar = nullptr, *dy = nullptr;
+    float *x32 = nullptr, *xhat32 = nullptr, *y32 = nullptr;   // FP32-form iterates
+    int form = 0;                 // form of the iterates during a solve (0 FP64, 1 FP32)
     double *xo = nullptr, *yo = nullptr, *zo = nullptr;
 
     // reductions and control
@@ -318,6 +327,7 @@ void free_all(hpr_ctx *c)
     void *dev[] = {c->A_rp, c->A_ci, c->A_val, c->T_rp, c->T_ci, c->T_perm, c->T_val,
                    c->SA.srow, c->SA.sptr, c->SA.wstart, c->SA.slg, c->SA.col, c->SA.val, c->SA.src,
                    c->ST.srow, c->ST.sptr, c->ST.wstart, c->ST.slg, c->ST.col, c->ST.val, c->ST.src,
+                   c->SA.val32, c->ST.val32, c->x32, c->xhat32, c->y32,
                    c->perm_r, c->perm_c, c->ineq, c->bp, c->cp, c->lp, c->up, c->wrp, c->wcp,
                    c->unperm, c->Dr, c->Dc, c->wr, c->wc, c->b_s, c->c_s,
                    c->l_s, c->u_s, c->l_o, c->u_o, c->x, c->x0, c->xhat, c->xbar,
@@ -359,12 +369,12 @@ int launch_reduce(hpr_ctx *ctx, const std::vector<std::pair<int, int>> &qc, doub
     return HPR_OK;
 }
 
-SellArgs sell_of(hpr_ctx *ctx, const SellDev &d, const int *skip = nullptr)
+SellArgs sell_of(const SellDev &d, bool fp32, const int *skip = nullptr)
 {
-    (void)ctx;
     SellArgs a;
     a.rows = d.rows; a.nslices = d.nslices; a.srow = d.srow; a.sptr = d.sptr; a.slg = d.slg;
-    a.wstart = d.wstart; a.val = d.val; a.col = d.col; a.skip = skip;
+    a.wstart = d.wstart; a.col = d.col; a.skip = skip;
+    a.val = fp32 ? (const void *)d.val32 : (const void *)d.val;
     return a;
 }
 
@@ -384,7 +394,7 @@ template <class E>
 int launch_sell(hpr_ctx *ctx, const SellDev &M, int grid, const E &e, const int *skip = nullptr)
 {
     if (M.rows == 0) return HPR_OK;
-    k_sell<E><<<grid, TB, 0, ctx->stream>>>(sell_of(ctx, M, skip), e);
+    k_sell<E><<<grid, TB, 0, ctx->stream>>>(sell_of(M, sizeof(typename E::Val) == 4, skip), e);
     CKL();
     ctx->launches += 1;
     return HPR_OK;
@@ -415,6 +425,31 @@ EpiY<CHECK> epi_y(hpr_ctx *c, int it)
     return e;
 }
 
+template <bool CHECK>
+EpiX32<CHECK> epi_x32(hpr_ctx *c, int it)
+{
+    EpiX32<CHECK> e{};
+    e.xa = c->y32; e.xb = c->y32;
+    e.q[0] = Q_DX2; e.q[1] = Q_XX0; e.q[2] = Q_CX; e.q[3] = Q_BND;
+    e.partials = c->partials; e.pstride = c->pstride;
+    e.c = c->cp; e.l = c->lp; e.u = c->up; e.x0 = c->x0;
+    e.x = c->x32; e.xhat = c->xhat32; e.xbar = c->xbar; e.zbar = c->zbar; e.dx = c->dx;
+    e.ctl = c->ctl; e.it = it;
+    return e;
+}
+
+template <bool CHECK>
+EpiY32<CHECK> epi_y32(hpr_ctx *c, int it)
+{
+    EpiY32<CHECK> e{};
+    e.xa = c->xhat32; e.xb = c->xhat32;
+    e.q[0] = Q_DY2; e.q[1] = Q_YY0; e.q[2] = Q_BY;
+    e.partials = c->partials; e.pstride = c->pstride;
+    e.b = c->bp; e.y0 = c->y0; e.y = c->y32; e.ybar = c->ybar; e.dy = c->dy;
+    e.ctl = c->ctl; e.it = it; e.ineq = c->ineq;
+    return e;
+}
+
 EpiNorm epi_norm(hpr_ctx *c, const double *xin, double *out, int q)
 {
     EpiNorm e{};
@@ -429,7 +464,15 @@ int enqueue_iteration(hpr_ctx *ctx, int it, bool store, bool check, int slot)
 {
     int st;
     const Grids &g = ctx->grids;
-    if (store || check) {
+    if (ctx->form == 1) {
+        if (store || check) {
+            if ((st = launch_sell(ctx, ctx->ST, g.Xc, epi_x32<true>(ctx, it)))) return st;
+            if ((st = launch_sell(ctx, ctx->SA, g.Yc, epi_y32<true>(ctx, it)))) return st;
+        } else {
+            if ((st = launch_sell(ctx, ctx->ST, g.X, epi_x32<false>(ctx, it)))) return st;
+            if ((st = launch_sell(ctx, ctx->SA, g.Y, epi_y32<false>(ctx, it)))) return st;
+        }
+    } else if (store || check) {
         if ((st = launch_sell(ctx, ctx->ST, g.Xc, epi_x<true>(ctx, it)))) return st;
         if ((st = launch_sell(ctx, ctx->SA, g.Yc, epi_y<true>(ctx, it)))) return st;
     } else {
@@ -472,10 +515,18 @@ int trace_copy(hpr_ctx *ctx, int64_t k)
     const int64_t n = ctx->n, m = ctx->m;
     double *rec = ctx->trace + (size_t)k * (size_t)(3 * n + 2 * m);
     CK(cudaMemcpyAsync(rec, ctx->xbar, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(rec + n, ctx->xhat, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(rec + 2 * n, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemcpyAsync(rec + 3 * n, ctx->ybar, sizeof(double) * m, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(rec + 3 * n + m, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (ctx->form == 1) {
+        // FP32-form iterates, widened into the record
+        k_widen<<<grid_for(2 * n), 256, 0, ctx->stream>>>((int)n, (int)n, ctx->xhat32, ctx->x32, rec + n, rec + 2 * n);
+        CKL();
+        k_widen<<<grid_for(m), 256, 0, ctx->stream>>>(0, (int)m, ctx->x32, ctx->y32, nullptr, rec + 3 * n + m);
+        CKL();
+    } else {
+        CK(cudaMemcpyAsync(rec + n, ctx->xhat, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(rec + 2 * n, ctx->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(rec + 3 * n + m, ctx->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     ctx->trace_written = std::max(ctx->trace_written, k + 1);
     return HPR_OK;
 }
@@ -642,12 +693,18 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
         if ((r = setup_kernel<EpiDual>(ctx, &g.Dual))) return r;
         if ((r = setup_kernel<EpiPrimal>(ctx, &g.Primal))) return r;
         if ((r = setup_kernel<EpiNorm>(ctx, &g.Norm))) return r;
+        int dummy;
+        if ((r = setup_kernel<EpiX32<false>>(ctx, &dummy))) return r;
+        if ((r = setup_kernel<EpiX32<true>>(ctx, &dummy))) return r;
+        if ((r = setup_kernel<EpiY32<false>>(ctx, &dummy))) return r;
+        if ((r = setup_kernel<EpiY32<true>>(ctx, &dummy))) return r;
         ctx->pstride = std::max({g.X, g.Xc, g.Y, g.Yc, g.Dual, g.Primal, g.Norm,
                                  (int)((std::max(m, n) + TB - 1) / TB), 1});
     }
     auto upload_sell = [&](SellDev &D, const SellHost &H, int rows) -> int {
         D.rows = rows; D.nslices = H.nslices;
         D.entries = (int64_t)H.col.size();
+        DALLOC(D.val32, D.entries);
         DALLOC(D.srow, (int64_t)H.srow.size()); DALLOC(D.sptr, (int64_t)H.sptr.size());
         DALLOC(D.wstart, (int64_t)H.wstart.size()); DALLOC(D.slg, (int64_t)H.slg.size());
         DALLOC(D.col, D.entries); DALLOC(D.val, D.entries); DALLOC(D.src, D.entries);
@@ -672,6 +729,7 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
 
     DALLOC(ctx->bp, m); DALLOC(ctx->wrp, m); DALLOC(ctx->cp, n); DALLOC(ctx->lp, n); DALLOC(ctx->up, n);
     DALLOC(ctx->wcp, n); DALLOC(ctx->unperm, n + m);
+    DALLOC(ctx->x32, n); DALLOC(ctx->xhat32, n); DALLOC(ctx->y32, m);
     DALLOC(ctx->Dr, m); DALLOC(ctx->Dc, n); DALLOC(ctx->wr, m); DALLOC(ctx->wc, n);
     DALLOC(ctx->b_s, m); DALLOC(ctx->c_s, n); DALLOC(ctx->l_s, n); DALLOC(ctx->u_s, n);
     DALLOC(ctx->l_o, n); DALLOC(ctx->u_o, n);
@@ -747,6 +805,8 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     // the iteration's copies: stored values through the position map, vectors renumbered
     k_gather_src<<<grid_for(ctx->SA.entries), 256, 0, s>>>(ctx->SA.entries, ctx->A_val, ctx->SA.src, ctx->SA.val); CKL();
     k_gather_src<<<grid_for(ctx->ST.entries), 256, 0, s>>>(ctx->ST.entries, ctx->T_val, ctx->ST.src, ctx->ST.val); CKL();
+    k_narrow<<<grid_for(ctx->SA.entries), 256, 0, s>>>(ctx->SA.entries, ctx->SA.val, ctx->SA.val32); CKL();
+    k_narrow<<<grid_for(ctx->ST.entries), 256, 0, s>>>(ctx->ST.entries, ctx->ST.val, ctx->ST.val32); CKL();
     k_permute<<<gm, 256, 0, s>>>(m, ctx->b_s, ctx->perm_r, ctx->bp); CKL();
     k_permute<<<gm, 256, 0, s>>>(m, ctx->wr, ctx->perm_r, ctx->wrp); CKL();
     k_permute<<<gn, 256, 0, s>>>(n, ctx->c_s, ctx->perm_c, ctx->cp); CKL();
@@ -794,6 +854,8 @@ int hpr_default_options(hpr_options *o)
     o->use_graph = 1;
     o->verbose = 0;
     o->cuda_stream = nullptr;
+    o->precision = 0;
+    o->switch_tol = 1e-5;
     return HPR_OK;
 }
 
@@ -808,6 +870,8 @@ static int check_options(hpr_ctx *ctx, const hpr_options *o)
     if (o->power_max_iter < 1) return fail_arg(ctx, HPR_ERR_ARG, "power_max_iter must be >= 1");
     if (o->trace_iters < 0) return fail_arg(ctx, HPR_ERR_ARG, "trace_iters must be >= 0");
     if (!(o->lambda_fixed >= 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "lambda_fixed must be >= 0");
+    if (o->precision != 0 && o->precision != 1) return fail_arg(ctx, HPR_ERR_ARG, "precision must be 0 or 1");
+    if (!(o->switch_tol >= 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "switch_tol must be >= 0");
     return HPR_OK;
 }
 
@@ -984,6 +1048,10 @@ int hpr_solve(hpr_ctx *ctx, double tol)
     CK(cudaMemsetAsync(ctx->x0, 0, sizeof(double) * n, s));
     CK(cudaMemsetAsync(ctx->y, 0, sizeof(double) * m, s));
     CK(cudaMemsetAsync(ctx->y0, 0, sizeof(double) * m, s));
+    CK(cudaMemsetAsync(ctx->x32, 0, sizeof(float) * n, s));
+    CK(cudaMemsetAsync(ctx->y32, 0, sizeof(float) * m, s));
+    ctx->form = (int)o.precision;
+    int64_t iters_fp32 = 0;
 
     double sigma = o.sigma0;
     int64_t k = 0, t = 0, r = 0;
@@ -1025,7 +1093,7 @@ int hpr_solve(hpr_ctx *ctx, double tol)
                 }
             }
         } else if (o.use_graph) {
-            const GraphKey key{L, first_r0 ? 1 : 0};
+            const GraphKey key{L, first_r0 ? 1 : 0, ctx->form};
             auto itg = ctx->graphs.find(key);
             if (itg == ctx->graphs.end()) {
                 CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -1127,11 +1195,26 @@ int hpr_solve(hpr_ctx *ctx, double tol)
                     (long long)(kk + 1), (long long)r, (long long)tl, sigma, kkt, errp, errd, gap, Rt,
                     cause, elapsed);
 
-        if (restart) {
+        if (ctx->form == 1) iters_fp32 = kk + 1;
+        // the FP32 form hands over to FP64 iterates at the first check below switch_tol
+        const bool widen = ctx->form == 1 && !stop && kkt < o.switch_tol;
+        if (widen) ctx->form = 0;
+        if (restart && ctx->form == 1) {
+            k_restart32<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->xbar, ctx->ybar, ctx->x32,
+                                                        ctx->x0, ctx->y32, ctx->y0);
+            CKL();
+            ctx->launches += 1;
+        } else if (restart) {
             k_restart<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->xbar, ctx->ybar, ctx->x,
                                                       ctx->x0, ctx->y, ctx->y0);
             CKL();
             ctx->launches += 1;
+        } else if (widen) {
+            k_widen<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->x32, ctx->y32, ctx->x, ctx->y);
+            CKL();
+            ctx->launches += 1;
+        }
+        if (restart) {
             sigma = sigma_next;
             t = 0;
             r++;
@@ -1167,6 +1250,7 @@ int hpr_solve(hpr_ctx *ctx, double tol)
     I.time_to_1e4_s = time_1e4; I.iters_to_1e4 = iters_1e4;
     I.iters = k; I.restarts = r; I.power_iters = ctx->power_iters;
     I.n_checks = (int64_t)ctx->checks.size(); I.launches = ctx->launches; I.status = status;
+    I.iters_fp32 = iters_fp32;
     ctx->solved = true;
     return status;
 }
@@ -1260,10 +1344,15 @@ int hpr_time_iteration(hpr_ctx *ctx, int64_t reps, double *ms_x, double *ms_y, d
     float a = 0.f, b = 0.f;
     int rc = HPR_OK;
     for (int64_t r = 0; r < reps && rc == HPR_OK; ++r) {
+        const bool f32 = ctx->opt.precision == 1;
         cudaEventRecord(ev[0], s);
-        if ((rc = launch_sell(ctx, ctx->ST, ctx->grids.X, epi_x<false>(ctx, 0)))) break;
+        rc = f32 ? launch_sell(ctx, ctx->ST, ctx->grids.X, epi_x32<false>(ctx, 0))
+                 : launch_sell(ctx, ctx->ST, ctx->grids.X, epi_x<false>(ctx, 0));
+        if (rc) break;
         cudaEventRecord(ev[1], s);
-        if ((rc = launch_sell(ctx, ctx->SA, ctx->grids.Y, epi_y<false>(ctx, 0)))) break;
+        rc = f32 ? launch_sell(ctx, ctx->SA, ctx->grids.Y, epi_y32<false>(ctx, 0))
+                 : launch_sell(ctx, ctx->SA, ctx->grids.Y, epi_y<false>(ctx, 0));
+        if (rc) break;
         cudaEventRecord(ev[2], s);
         cudaError_t e = cudaEventSynchronize(ev[2]);
         if (e != cudaSuccess) { rc = fail_cuda(ctx, e, "hpr_time_iteration", __LINE__); break; }

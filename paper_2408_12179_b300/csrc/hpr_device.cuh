@@ -120,6 +120,59 @@ __device__ __forceinline__ double pos_part(double v)
 // the warps of the grid in contiguous runs of about equal cost (host-made table) that
 // keep light groups whole and split heavy ones by slice; consecutive runs go to
 // different CTAs.
+// Row accumulators.  Acc<double>: FP64 FMA.  Acc<float> (the FP32 form): the FP32 product
+// a*b is split exactly into p + e (e = fma(a, b, -p)) and accumulated in double-float
+// (hi, lo) with Knuth's TwoSum, so a row sum of FP32 products keeps ~48 bits without a
+// single FP64 instruction; the row's value is hi + lo in FP64.  Explicit round-to-nearest
+// intrinsics keep the compiler from contracting the error-free transformations.
+template <class V>
+struct Acc;
+
+template <>
+struct Acc<double> {
+    double a = 0.0;
+    __device__ __forceinline__ void add(double v, double g) { a = fma(v, g, a); }
+    __device__ __forceinline__ void merge(const Acc &o) { a += o.a; }
+    __device__ __forceinline__ void xor_reduce(int o) { a += __shfl_xor_sync(0xffffffffu, a, o); }
+    __device__ __forceinline__ double value() const { return a; }
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+template <>
+struct Acc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float v, float g)
+    {
+        const float p = __fmul_rn(v, g);
+        const float pe = __fmaf_rn(v, g, -p);     // exact: v*g = p + pe
+        float s, e;
+        two_sum(hi, p, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(e, pe));
+    }
+    __device__ __forceinline__ void merge(const Acc &o)
+    {
+        float s, e;
+        two_sum(hi, o.hi, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(e, o.lo));
+    }
+    __device__ __forceinline__ void xor_reduce(int o)
+    {
+        Acc t;
+        t.hi = __shfl_xor_sync(0xffffffffu, hi, o);
+        t.lo = __shfl_xor_sync(0xffffffffu, lo, o);
+        merge(t);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 struct SellArgs {
     int rows;             // rows of the matrix (in the renumbered order)
     int nslices;
@@ -127,17 +180,19 @@ struct SellArgs {
     const int *sptr;      // nslices + 1: first stored entry; slice s has (sptr[s+1]-sptr[s])/32 steps
     const unsigned char *slg;   // log2 of the lanes per row of each slice
     const int *wstart;    // runs + 1: run i covers slices [wstart[i], wstart[i+1])
-    const double *val;    // stored values (padding: 0)
+    const void *val;      // stored values, double or float (E::Val); padding: 0
     const int *col;       // stored column indices (padding: 0)
     const int *skip;      // optional: the kernel does nothing while *skip != 0
 };
 
-// E supplies NV gathered vectors xa (, xb), NP partial sums (ids q[]), a Pre record of
-// epilogue operands (prefetch(j)) and row(j, act, s, pre, part).
+// E supplies the value type Val (double or float) of the stored values and gathered
+// vectors, NV gathered vectors xa (, xb), NP partial sums (ids q[]), a Pre record of
+// epilogue operands (prefetch(j)) and row(j, act, s, pre, part) with FP64 row sums s.
 template <class E>
 __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
 {
     constexpr int NV = E::NV, NP = E::NP;
+    using V = typename E::Val;
     __shared__ double red[TB / 32];
     if (S.skip && *S.skip) return;
     E ee = e;
@@ -167,12 +222,12 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
             buf_r0 = r0;                          // operands of the next 32 rows, early
             pre = ee.prefetch(min(r0 + lane, S.rows - 1));
         }
-        const double *pv = S.val + base + lane;
+        const V *pv = static_cast<const V *>(S.val) + base + lane;
         const int *pc = S.col + base + lane;
-        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+        Acc<V> a0, a1, b0, b1;
         int k = 0;
         for (; k + 4 <= steps; k += 4) {
-            double v[4], g0[4], g1[4];
+            V v[4], g0[4], g1[4];
             int c[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -185,35 +240,35 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
                 if (NV == 2) g1[u] = __ldg(ee.xb + c[u]);
             }
             // two chains (even / odd steps) halve the dependent FMA latency
-            a0 = fma(v[0], g0[0], a0);
-            a1 = fma(v[1], g0[1], a1);
-            a0 = fma(v[2], g0[2], a0);
-            a1 = fma(v[3], g0[3], a1);
+            a0.add(v[0], g0[0]);
+            a1.add(v[1], g0[1]);
+            a0.add(v[2], g0[2]);
+            a1.add(v[3], g0[3]);
             if (NV == 2) {
-                b0 = fma(v[0], g1[0], b0);
-                b1 = fma(v[1], g1[1], b1);
-                b0 = fma(v[2], g1[2], b0);
-                b1 = fma(v[3], g1[3], b1);
+                b0.add(v[0], g1[0]);
+                b1.add(v[1], g1[1]);
+                b0.add(v[2], g1[2]);
+                b1.add(v[3], g1[3]);
             }
         }
         for (; k < steps; ++k) {
-            const double v = __ldcs(pv + k * 32);
+            const V v = __ldcs(pv + k * 32);
             const int c = __ldcs(pc + k * 32);
-            a0 = fma(v, __ldg(ee.xa + c), a0);
-            if (NV == 2) b0 = fma(v, __ldg(ee.xb + c), b0);
+            a0.add(v, __ldg(ee.xa + c));
+            if (NV == 2) b0.add(v, __ldg(ee.xb + c));
         }
         if (steps >= 4) {                         // warp-uniform
-            a0 += a1;
-            if (NV == 2) b0 += b1;
+            a0.merge(a1);
+            if (NV == 2) b0.merge(b1);
         }
         for (int o = 1; o < (1 << lg); o <<= 1) { // warp-uniform: lg is per slice
-            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-            if (NV == 2) b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+            a0.xor_reduce(o);
+            if (NV == 2) b0.xor_reduce(o);
         }
         // row q of this slice (held by lanes q*L ...) moves to lane buf_n + q
         const int src = (int)(((unsigned)(lane - buf_n) << lg) & 31u);
-        const double m0 = __shfl_sync(0xffffffffu, a0, src);
-        const double m1 = NV == 2 ? __shfl_sync(0xffffffffu, b0, src) : 0.0;
+        const double m0 = __shfl_sync(0xffffffffu, a0.value(), src);
+        const double m1 = NV == 2 ? __shfl_sync(0xffffffffu, b0.value(), src) : 0.0;
         if (lane >= buf_n && lane < buf_n + nrows) {
             buf0 = m0;
             buf1 = m1;
@@ -241,6 +296,7 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
 // check mode also stores x_bar, z_bar (eq. update-z), x - x_bar and the partial sums
 template <bool CHECK>
 struct EpiX {
+    using Val = double;
     static constexpr int NV = 1, NP = CHECK ? 4 : 0;
     const double *xa, *xb;       // gathered: y
     int q[4];
@@ -292,6 +348,7 @@ struct EpiX {
 // stores y_bar, y - y_bar and the partial sums
 template <bool CHECK>
 struct EpiY {
+    using Val = double;
     static constexpr int NV = 1, NP = CHECK ? 3 : 0;
     const double *xa, *xb;       // gathered: x_hat
     int q[3];
@@ -333,8 +390,105 @@ struct EpiY {
     }
 };
 
+// The FP32 form (FP32 stored values and FP32 iterates x, x_hat, y; FP64 anchors, data,
+// epilogue arithmetic and checks): phase X.  Row sums arrive in FP64 from the
+// double-float accumulators; x and x_hat are rounded to FP32 when stored.
+template <bool CHECK>
+struct EpiX32 {
+    using Val = float;
+    static constexpr int NV = 1, NP = CHECK ? 4 : 0;
+    const float *xa, *xb;        // gathered: y (FP32)
+    int q[4];
+    double *partials;
+    int pstride;
+    const double *c, *l, *u, *x0;
+    float *x, *xhat;
+    double *xbar, *zbar, *dx;
+    const DevCtl *ctl;
+    int it;
+    double sigma, ha, hb;
+    struct Pre { double x0, c, l, u; float x; };
+    __device__ __forceinline__ void load()
+    {
+        sigma = ctl->sigma;
+        ha = ctl->h[2 * it];
+        hb = ctl->h[2 * it + 1];
+    }
+    __device__ __forceinline__ Pre prefetch(int j) const { return Pre{x0[j], c[j], l[j], u[j], x[j]}; }
+    __device__ __forceinline__ void row(int j, bool act, const double *s, const Pre &p,
+                                        double *part) const
+    {
+        const double xj = (double)p.x;
+        const double v = fma(sigma, s[0] - p.c, xj);
+        const double xb_ = clamp_lu(v, p.l, p.u);
+        const double xh = fma(2.0, xb_, -xj);
+        const double xn = fma(hb, xh, ha * p.x0);
+        if (act) {
+            xhat[j] = (float)xh;
+            x[j] = (float)xn;
+        }
+        if (CHECK && act) {
+            const double zb = (xb_ - v) / sigma;
+            const double dd = xj - xb_;
+            xbar[j] = xb_;
+            zbar[j] = zb;
+            dx[j] = dd;
+            part[0] = fma(dd, dd, part[0]);
+            part[1] = fma(xb_ - p.x0, xb_ - p.x0, part[1]);
+            part[2] = fma(p.c, xb_, part[2]);
+            if (zb > 0.0) part[3] = fma(zb, p.l, part[3]);
+            else if (zb < 0.0) part[3] = fma(zb, p.u, part[3]);
+        }
+    }
+};
+
+// the FP32 form, phase Y
+template <bool CHECK>
+struct EpiY32 {
+    using Val = float;
+    static constexpr int NV = 1, NP = CHECK ? 3 : 0;
+    const float *xa, *xb;        // gathered: x_hat (FP32)
+    int q[3];
+    double *partials;
+    int pstride;
+    const double *b, *y0;
+    float *y;
+    double *ybar, *dy;
+    const DevCtl *ctl;
+    int it;
+    const unsigned char *ineq;
+    double inv_ls, ha, hb;
+    struct Pre { double b, y0; float y; unsigned char ineq; };
+    __device__ __forceinline__ void load()
+    {
+        inv_ls = ctl->inv_ls;
+        ha = ctl->h[2 * it];
+        hb = ctl->h[2 * it + 1];
+    }
+    __device__ __forceinline__ Pre prefetch(int i) const { return Pre{b[i], y0[i], y[i], ineq[i]}; }
+    __device__ __forceinline__ void row(int i, bool act, const double *s, const Pre &p,
+                                        double *part) const
+    {
+        const double yi = (double)p.y;
+        double yb = fma(p.b - s[0], inv_ls, yi);
+        if (p.ineq) yb = pos_part(yb);
+        const double yh = fma(2.0, yb, -yi);
+        const double yn = fma(hb, yh, ha * p.y0);
+        if (act) y[i] = (float)yn;
+        if (CHECK && act) {
+            const double dd = yi - yb;
+            ybar[i] = yb;
+            dy[i] = dd;
+            part[0] = fma(dd, dd, part[0]);
+            part[1] = fma(yb - p.y0, yb - p.y0, part[1]);
+            part[2] = fma(p.b, yb, part[2]);
+        }
+    }
+};
+
 // dual residual of Section 4.1 in original-space weights w_c = beta_c / D_c
 struct EpiDual {
+    using Val = double;
     static constexpr int NV = 1, NP = 1;
     const double *xa, *xb;       // gathered: y_bar
     int q[1];
@@ -354,6 +508,7 @@ struct EpiDual {
 // primal residual with weights w_r = beta_b / D_r and the cross term <dy, A dx> of the
 // M-norm (eq. def:M with T1 = lambda I - A A^*)
 struct EpiPrimal {
+    using Val = double;
     static constexpr int NV = 2, NP = 2;
     const double *xa, *xb;       // gathered: x_bar, x - x_bar
     int q[2];
@@ -378,6 +533,7 @@ struct EpiPrimal {
 
 // power method: out = M xin and the partial ||out||^2
 struct EpiNorm {
+    using Val = double;
     static constexpr int NV = 1, NP = 1;
     const double *xa, *xb;
     int q[1];
@@ -433,6 +589,41 @@ __global__ void k_restart(int n, int m, const double *__restrict__ xbar,
             y0[i - n] = v;
         }
     }
+}
+
+// restart in the FP32 form: x = (float) x_bar, x0 = x_bar, y likewise
+__global__ void k_restart32(int n, int m, const double *__restrict__ xbar,
+                            const double *__restrict__ ybar, float *x, double *x0, float *y,
+                            double *y0)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            const double v = xbar[i];
+            x[i] = (float)v;
+            x0[i] = v;
+        } else {
+            const double v = ybar[i - n];
+            y[i - n] = (float)v;
+            y0[i - n] = v;
+        }
+    }
+}
+
+// switch from the FP32 form to FP64 iterates: x = (double) x32, y = (double) y32
+__global__ void k_widen(int n, int m, const float *__restrict__ x32, const float *__restrict__ y32,
+                        double *x, double *y)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+        if (i < n) x[i] = (double)x32[i];
+        else y[i - n] = (double)y32[i - n];
+    }
+}
+
+// FP32 copy of FP64 values (round to nearest)
+__global__ void k_narrow(int64_t len, const double *__restrict__ src, float *dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
 }
 
 // back-map of w_bar (renumbered) to the original LP in its original order:

@@ -42,7 +42,8 @@ class hpr_options(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("lambda_fixed", ctypes.c_double),
                 ("restart", ctypes.c_int64), ("sigma_update", ctypes.c_int64),
                 ("trace_iters", ctypes.c_int64), ("use_graph", ctypes.c_int64),
-                ("verbose", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p)]
+                ("verbose", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
+                ("precision", ctypes.c_int64), ("switch_tol", ctypes.c_double)]
 
 
 class hpr_info(ctypes.Structure):
@@ -54,7 +55,8 @@ class hpr_info(ctypes.Structure):
                 ("time_to_1e4_s", ctypes.c_double), ("iters_to_1e4", ctypes.c_int64),
                 ("iters", ctypes.c_int64), ("restarts", ctypes.c_int64),
                 ("power_iters", ctypes.c_int64), ("n_checks", ctypes.c_int64),
-                ("launches", ctypes.c_int64), ("status", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("status", ctypes.c_int64),
+                ("iters_fp32", ctypes.c_int64)]
 
 
 class hpr_check_record(ctypes.Structure):
