@@ -48,14 +48,13 @@ struct GraphKey {
 
 }  // namespace
 
-struct Grids {
-    int X, Xc, Y, Yc, Dual, Primal, Norm;   // grid of each sliced-ELL kernel (all CTAs resident)
-};
 
 // one matrix in the sliced-ELL layout (device arrays; see k_sell)
 struct SellDev {
     int rows = 0, nslices = 0;
     int64_t entries = 0;          // stored entries (nonzeros + padding)
+    int nruns = 0;                // work units (one per warp)
+    int grid = 0;                 // CTAs of a sliced-ELL launch: ceil(nruns / warps per CTA)
     int *srow = nullptr, *sptr = nullptr, *wstart = nullptr, *col = nullptr;
     unsigned char *slg = nullptr;
     double *val = nullptr;
@@ -80,7 +79,6 @@ struct hpr_ctx {
     int *perm_r = nullptr;        // renumbered row i of A is original row perm_r[i]
     int *perm_c = nullptr;        // renumbered column j is original column perm_c[j]
     unsigned char *ineq = nullptr;// renumbered row i belongs to A2 (m2 block)
-    Grids grids{};
     int num_sms = 0;
 
     // vectors (device)
@@ -205,9 +203,10 @@ std::vector<int> order_by_length(const std::vector<int> &rp, int rows)
 // renamed by icol): host index arrays; the values are gathered on the GPU through `src`.
 // Rows are taken in groups of 32; a group uses L lanes per row, L the smallest power of
 // two that keeps its widest slice within SELL_STEPS steps (L <= 32), and is stored as L
-// slices of 32 / L rows.  Groups are then split over `runs` warps in contiguous runs of
-// about equal cost.
+// slices of 32 / L rows.  Work units (one per warp): a group whole, or each slice of a
+// group whose cost exceeds UNIT_COST.
 constexpr int SELL_STEPS = 40;
+constexpr double UNIT_COST = 64.0;
 
 struct SellHost {
     int nslices = 0;
@@ -216,7 +215,7 @@ struct SellHost {
 };
 
 SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int rows,
-                    const std::vector<int> &perm, const std::vector<int> &icol, int runs)
+                    const std::vector<int> &perm, const std::vector<int> &icol)
 {
     SellHost h;
     auto len = [&](int i) { return rp[(size_t)perm[(size_t)i] + 1] - rp[(size_t)perm[(size_t)i]]; };
@@ -253,35 +252,18 @@ SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int 
         }
     }
     gfirst.push_back(h.nslices);
-    // work units: a light group whole, a heavy group (costlier than an average run) by
-    // slice; then contiguous runs of units of about equal cost
-    double total = 0.0;
-    for (double c : scost) total += c;
-    const double target = total / (double)runs;
-    std::vector<int> ustart;
-    std::vector<double> ucost;
+    // work units: a light group whole, a heavy group by slice
+    h.wstart.clear();
     for (size_t g = 0; g + 1 < gfirst.size(); ++g) {
         double gc = 0.0;
         for (int sl = gfirst[g]; sl < gfirst[g + 1]; ++sl) gc += scost[(size_t)sl];
-        if (gc <= target) {
-            ustart.push_back(gfirst[g]);
-            ucost.push_back(gc);
+        if (gc <= UNIT_COST) {
+            h.wstart.push_back(gfirst[g]);
         } else {
-            for (int sl = gfirst[g]; sl < gfirst[g + 1]; ++sl) {
-                ustart.push_back(sl);
-                ucost.push_back(scost[(size_t)sl]);
-            }
+            for (int sl = gfirst[g]; sl < gfirst[g + 1]; ++sl) h.wstart.push_back(sl);
         }
     }
-    ustart.push_back(h.nslices);
-    h.wstart.assign((size_t)runs + 1, h.nslices);
-    h.wstart[0] = 0;
-    double acc = 0.0;
-    int wi = 1;
-    for (size_t u = 0; u + 1 < ustart.size() && wi < runs; ++u) {
-        acc += ucost[u];
-        while (wi < runs && acc >= total * (double)wi / (double)runs) h.wstart[(size_t)wi++] = ustart[u + 1];
-    }
+    h.wstart.push_back(h.nslices);
     return h;
 }
 
@@ -373,28 +355,26 @@ SellArgs sell_of(const SellDev &d, bool fp32, const int *skip = nullptr)
 {
     SellArgs a;
     a.rows = d.rows; a.nslices = d.nslices; a.srow = d.srow; a.sptr = d.sptr; a.slg = d.slg;
-    a.wstart = d.wstart; a.col = d.col; a.skip = skip;
+    a.wstart = d.wstart; a.nruns = d.nruns; a.col = d.col; a.skip = skip;
     a.val = fp32 ? (const void *)d.val32 : (const void *)d.val;
     return a;
 }
 
-// every k_sell instance runs on the same grid (the slice-to-warp table depends on it):
-// SELL_CTAS_PER_SM CTAs of 256 threads per SM, all resident (launch bounds)
+// every k_sell instance must fit at least one CTA on an SM (its launch bounds)
 template <class E>
-int setup_kernel(hpr_ctx *ctx, int *grid)
+int check_kernel(hpr_ctx *ctx)
 {
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sell<E>, TB, 0));
-    if (per_sm < SELL_CTAS_PER_SM) return fail_arg(ctx, HPR_ERR_CUDA, "sliced-ELL kernel does not fit its CTAs on an SM");
-    *grid = SELL_CTAS_PER_SM * ctx->num_sms;
+    if (per_sm < 1) return fail_arg(ctx, HPR_ERR_CUDA, "sliced-ELL kernel does not fit on an SM");
     return HPR_OK;
 }
 
 template <class E>
-int launch_sell(hpr_ctx *ctx, const SellDev &M, int grid, const E &e, const int *skip = nullptr)
+int launch_sell(hpr_ctx *ctx, const SellDev &M, const E &e, const int *skip = nullptr)
 {
     if (M.rows == 0) return HPR_OK;
-    k_sell<E><<<grid, TB, 0, ctx->stream>>>(sell_of(M, sizeof(typename E::Val) == 4, skip), e);
+    k_sell<E><<<M.grid, TB, 0, ctx->stream>>>(sell_of(M, sizeof(typename E::Val) == 4, skip), e);
     CKL();
     ctx->launches += 1;
     return HPR_OK;
@@ -463,35 +443,34 @@ EpiNorm epi_norm(hpr_ctx *c, const double *xin, double *out, int q)
 int enqueue_iteration(hpr_ctx *ctx, int it, bool store, bool check, int slot)
 {
     int st;
-    const Grids &g = ctx->grids;
     if (ctx->form == 1) {
         if (store || check) {
-            if ((st = launch_sell(ctx, ctx->ST, g.Xc, epi_x32<true>(ctx, it)))) return st;
-            if ((st = launch_sell(ctx, ctx->SA, g.Yc, epi_y32<true>(ctx, it)))) return st;
+            if ((st = launch_sell(ctx, ctx->ST, epi_x32<true>(ctx, it)))) return st;
+            if ((st = launch_sell(ctx, ctx->SA, epi_y32<true>(ctx, it)))) return st;
         } else {
-            if ((st = launch_sell(ctx, ctx->ST, g.X, epi_x32<false>(ctx, it)))) return st;
-            if ((st = launch_sell(ctx, ctx->SA, g.Y, epi_y32<false>(ctx, it)))) return st;
+            if ((st = launch_sell(ctx, ctx->ST, epi_x32<false>(ctx, it)))) return st;
+            if ((st = launch_sell(ctx, ctx->SA, epi_y32<false>(ctx, it)))) return st;
         }
     } else if (store || check) {
-        if ((st = launch_sell(ctx, ctx->ST, g.Xc, epi_x<true>(ctx, it)))) return st;
-        if ((st = launch_sell(ctx, ctx->SA, g.Yc, epi_y<true>(ctx, it)))) return st;
+        if ((st = launch_sell(ctx, ctx->ST, epi_x<true>(ctx, it)))) return st;
+        if ((st = launch_sell(ctx, ctx->SA, epi_y<true>(ctx, it)))) return st;
     } else {
-        if ((st = launch_sell(ctx, ctx->ST, g.X, epi_x<false>(ctx, it)))) return st;
-        if ((st = launch_sell(ctx, ctx->SA, g.Y, epi_y<false>(ctx, it)))) return st;
+        if ((st = launch_sell(ctx, ctx->ST, epi_x<false>(ctx, it)))) return st;
+        if ((st = launch_sell(ctx, ctx->SA, epi_y<false>(ctx, it)))) return st;
     }
     if (!check) return HPR_OK;
     EpiDual d{};
     d.xa = ctx->ybar; d.xb = ctx->ybar; d.q[0] = Q_RD;
     d.partials = ctx->partials; d.pstride = ctx->pstride;
     d.c = ctx->cp; d.zbar = ctx->zbar; d.wc = ctx->wcp;
-    if ((st = launch_sell(ctx, ctx->ST, g.Dual, d))) return st;
+    if ((st = launch_sell(ctx, ctx->ST, d))) return st;
     EpiPrimal p{};
     p.xa = ctx->xbar; p.xb = ctx->dx; p.q[0] = Q_RP; p.q[1] = Q_CROSS;
     p.partials = ctx->partials; p.pstride = ctx->pstride;
     p.b = ctx->bp; p.wr = ctx->wrp; p.dy = ctx->dy; p.ineq = ctx->ineq;
-    if ((st = launch_sell(ctx, ctx->SA, g.Primal, p))) return st;
-    const int nX = ctx->ST.rows ? g.Xc : 0, nY = ctx->SA.rows ? g.Yc : 0;
-    const int nD = ctx->ST.rows ? g.Dual : 0, nP = ctx->SA.rows ? g.Primal : 0;
+    if ((st = launch_sell(ctx, ctx->SA, p))) return st;
+    const int nX = ctx->ST.rows ? ctx->ST.grid : 0, nY = ctx->SA.rows ? ctx->SA.grid : 0;
+    const int nD = nX, nP = nY;
     return launch_reduce(ctx, {{Q_DX2, nX}, {Q_XX0, nX}, {Q_CX, nX}, {Q_BND, nX},
                                {Q_DY2, nY}, {Q_YY0, nY}, {Q_BY, nY}, {Q_RD, nD},
                                {Q_RP, nP}, {Q_CROSS, nP}},
@@ -575,15 +554,15 @@ int run_power(hpr_ctx *ctx)
 
     auto enqueue_steps = [&](int steps) -> int {
         for (int k = 0; k < steps; ++k) {
-            int r = launch_sell(ctx, ctx->ST, ctx->grids.Norm, epi_norm(ctx, u, s, Q_S2), &ctx->pctl->done);
+            int r = launch_sell(ctx, ctx->ST, epi_norm(ctx, u, s, Q_S2), &ctx->pctl->done);
             if (r) return r;
-            r = launch_reduce(ctx, {{Q_S2, ctx->ST.rows ? ctx->grids.Norm : 0}}, ctx->scal, &ctx->pctl->done);
+            r = launch_reduce(ctx, {{Q_S2, ctx->ST.rows ? ctx->ST.grid : 0}}, ctx->scal, &ctx->pctl->done);
             if (r) return r;
             k_pow_after_s<<<1, 1, 0, ctx->stream>>>(ctx->pctl, ctx->scal);
             CKL();
-            r = launch_sell(ctx, ctx->SA, ctx->grids.Norm, epi_norm(ctx, s, w, Q_W2), &ctx->pctl->done);
+            r = launch_sell(ctx, ctx->SA, epi_norm(ctx, s, w, Q_W2), &ctx->pctl->done);
             if (r) return r;
-            r = launch_reduce(ctx, {{Q_W2, ctx->SA.rows ? ctx->grids.Norm : 0}}, ctx->scal, &ctx->pctl->done);
+            r = launch_reduce(ctx, {{Q_W2, ctx->SA.rows ? ctx->SA.grid : 0}}, ctx->scal, &ctx->pctl->done);
             if (r) return r;
             k_pow_after_w<<<1, 1, 0, ctx->stream>>>(ctx->pctl, ctx->scal);
             CKL();
@@ -678,31 +657,32 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     std::vector<int> ipr((size_t)m), ipc((size_t)n);
     for (int64_t i = 0; i < m; ++i) ipr[(size_t)pr[(size_t)i]] = (int)i;
     for (int64_t j = 0; j < n; ++j) ipc[(size_t)pc[(size_t)j]] = (int)j;
-    const int warps = SELL_CTAS_PER_SM * ctx->num_sms * (TB / 32);
-    SellHost hA = build_sell(rp, ci, (int)m, pr, ipc, warps);
-    SellHost hT = build_sell(trp, tci, (int)n, pc, ipr, warps);
+    SellHost hA = build_sell(rp, ci, (int)m, pr, ipc);
+    SellHost hT = build_sell(trp, tci, (int)n, pc, ipr);
     std::vector<unsigned char> ineq((size_t)m);
     for (int64_t i = 0; i < m; ++i) ineq[(size_t)i] = pr[(size_t)i] >= m1 ? 1 : 0;
     {
-        Grids &g = ctx->grids;
         int r;
-        if ((r = setup_kernel<EpiX<false>>(ctx, &g.X))) return r;
-        if ((r = setup_kernel<EpiX<true>>(ctx, &g.Xc))) return r;
-        if ((r = setup_kernel<EpiY<false>>(ctx, &g.Y))) return r;
-        if ((r = setup_kernel<EpiY<true>>(ctx, &g.Yc))) return r;
-        if ((r = setup_kernel<EpiDual>(ctx, &g.Dual))) return r;
-        if ((r = setup_kernel<EpiPrimal>(ctx, &g.Primal))) return r;
-        if ((r = setup_kernel<EpiNorm>(ctx, &g.Norm))) return r;
-        int dummy;
-        if ((r = setup_kernel<EpiX32<false>>(ctx, &dummy))) return r;
-        if ((r = setup_kernel<EpiX32<true>>(ctx, &dummy))) return r;
-        if ((r = setup_kernel<EpiY32<false>>(ctx, &dummy))) return r;
-        if ((r = setup_kernel<EpiY32<true>>(ctx, &dummy))) return r;
-        ctx->pstride = std::max({g.X, g.Xc, g.Y, g.Yc, g.Dual, g.Primal, g.Norm,
-                                 (int)((std::max(m, n) + TB - 1) / TB), 1});
+        if ((r = check_kernel<EpiX<false>>(ctx))) return r;
+        if ((r = check_kernel<EpiX<true>>(ctx))) return r;
+        if ((r = check_kernel<EpiY<false>>(ctx))) return r;
+        if ((r = check_kernel<EpiY<true>>(ctx))) return r;
+        if ((r = check_kernel<EpiDual>(ctx))) return r;
+        if ((r = check_kernel<EpiPrimal>(ctx))) return r;
+        if ((r = check_kernel<EpiNorm>(ctx))) return r;
+        if ((r = check_kernel<EpiX32<false>>(ctx))) return r;
+        if ((r = check_kernel<EpiX32<true>>(ctx))) return r;
+        if ((r = check_kernel<EpiY32<false>>(ctx))) return r;
+        if ((r = check_kernel<EpiY32<true>>(ctx))) return r;
     }
+    const int unitsA = (int)hA.wstart.size() - 1, unitsT = (int)hT.wstart.size() - 1;
+    const int gA = std::max(1, (unitsA + TB / 32 - 1) / (TB / 32));
+    const int gT = std::max(1, (unitsT + TB / 32 - 1) / (TB / 32));
+    ctx->pstride = std::max({gA, gT, (int)((std::max(m, n) + TB - 1) / TB), 1});
     auto upload_sell = [&](SellDev &D, const SellHost &H, int rows) -> int {
         D.rows = rows; D.nslices = H.nslices;
+        D.nruns = (int)H.wstart.size() - 1;
+        D.grid = std::max(1, (D.nruns + TB / 32 - 1) / (TB / 32));
         D.entries = (int64_t)H.col.size();
         DALLOC(D.val32, D.entries);
         DALLOC(D.srow, (int64_t)H.srow.size()); DALLOC(D.sptr, (int64_t)H.sptr.size());
@@ -1346,12 +1326,12 @@ int hpr_time_iteration(hpr_ctx *ctx, int64_t reps, double *ms_x, double *ms_y, d
     for (int64_t r = 0; r < reps && rc == HPR_OK; ++r) {
         const bool f32 = ctx->opt.precision == 1;
         cudaEventRecord(ev[0], s);
-        rc = f32 ? launch_sell(ctx, ctx->ST, ctx->grids.X, epi_x32<false>(ctx, 0))
-                 : launch_sell(ctx, ctx->ST, ctx->grids.X, epi_x<false>(ctx, 0));
+        rc = f32 ? launch_sell(ctx, ctx->ST, epi_x32<false>(ctx, 0))
+                 : launch_sell(ctx, ctx->ST, epi_x<false>(ctx, 0));
         if (rc) break;
         cudaEventRecord(ev[1], s);
-        rc = f32 ? launch_sell(ctx, ctx->SA, ctx->grids.Y, epi_y32<false>(ctx, 0))
-                 : launch_sell(ctx, ctx->SA, ctx->grids.Y, epi_y<false>(ctx, 0));
+        rc = f32 ? launch_sell(ctx, ctx->SA, epi_y32<false>(ctx, 0))
+                 : launch_sell(ctx, ctx->SA, epi_y<false>(ctx, 0));
         if (rc) break;
         cudaEventRecord(ev[2], s);
         cudaError_t e = cudaEventSynchronize(ev[2]);

@@ -116,10 +116,9 @@ __device__ __forceinline__ double pos_part(double v)
 // consecutive values per step (sliced ELL with a global sort; padding entries are
 // zeros).  A lane accumulates every L-th entry of its row with FMA; the L partial sums
 // of a row are added by a fixed xor butterfly and moved to the row's own lane, so the
-// epilogue of the group runs once, on 32 lanes, whatever L is.  The slices are split over
-// the warps of the grid in contiguous runs of about equal cost (host-made table) that
-// keep light groups whole and split heavy ones by slice; consecutive runs go to
-// different CTAs.
+// epilogue of the group runs once, on 32 lanes, whatever L is.  The work units are light
+// groups (whole) and the slices of heavy groups, longest first; each warp of the grid
+// takes one unit, so the hardware's CTA scheduler balances the load.
 // Row accumulators.  Acc<double>: FP64 FMA.  Acc<float> (the FP32 form): the FP32 product
 // a*b is split exactly into p + e (e = fma(a, b, -p)) and accumulated in double-float
 // (hi, lo) with Knuth's TwoSum, so a row sum of FP32 products keeps ~48 bits without a
@@ -179,7 +178,8 @@ struct SellArgs {
     const int *srow;      // nslices + 1: first row of each slice
     const int *sptr;      // nslices + 1: first stored entry; slice s has (sptr[s+1]-sptr[s])/32 steps
     const unsigned char *slg;   // log2 of the lanes per row of each slice
-    const int *wstart;    // runs + 1: run i covers slices [wstart[i], wstart[i+1])
+    int nruns;            // work units, one per warp
+    const int *wstart;    // nruns + 1: unit i covers slices [wstart[i], wstart[i+1])
     const void *val;      // stored values, double or float (E::Val); padding: 0
     const int *col;       // stored column indices (padding: 0)
     const int *skip;      // optional: the kernel does nothing while *skip != 0
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
     E ee = e;
     ee.load();
     const int lane = threadIdx.x & 31;
-    const int run = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // spreads runs over CTAs
+    const int run = blockIdx.x * (TB / 32) + (threadIdx.x >> 5);   // one unit per warp
     double part[NP > 0 ? NP : 1];
 #pragma unroll
     for (int i = 0; i < (NP > 0 ? NP : 1); ++i) part[i] = 0.0;
@@ -206,8 +206,9 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
     int buf_r0 = 0, buf_n = 0;                   // rows [buf_r0, buf_r0 + buf_n) hold sums
     double buf0 = 0.0, buf1 = 0.0;               // lane t: sum of row buf_r0 + t
     typename E::Pre pre{};
-    const int s_end = S.wstart[run + 1];
-    for (int s = S.wstart[run]; s < s_end; ++s) {
+    const int s_beg = run < S.nruns ? S.wstart[run] : 0;
+    const int s_end = run < S.nruns ? S.wstart[run + 1] : 0;
+    for (int s = s_beg; s < s_end; ++s) {
         const int lg = S.slg[s];
         const int r0 = S.srow[s], nrows = S.srow[s + 1] - r0;
         const int base = S.sptr[s];
