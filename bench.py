@@ -31,9 +31,9 @@ METRIC = ("time-to-KKT≤1e-8 (s), HPR iters/s, HBM GB/s % of peak; chosen form 
 # DRAM bytes per launch from one ncu capture of the full-size workload (see
 # profiles/), valid only for the kernel source they were taken on.
 NCU_TRAFFIC = {
-    "source_sha1": "d230f33a17e04b49215559660b92ba085a572803",
-    "k_phase_x": 88218623,
-    "k_phase_y": 72952576,
+    "source_sha1": "d257d2479f05cfb7fba2dc0092a1aeed8eab9650",
+    "k_phase_x": 87648512,
+    "k_phase_y": 73112064,
 }
 
 
@@ -70,7 +70,7 @@ class ClockSampler:
 
     FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,clocks.mem"
 
     def __init__(self, index):
         self.index = index
@@ -96,7 +96,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, mem, reasons = [], [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
@@ -107,13 +107,19 @@ class ClockSampler:
                 mx.append(float(parts[1]))
             except ValueError:
                 continue
+            for dst, v in ((pw, parts[2]), (mem, parts[8] if len(parts) > 8 else "")):
+                try:
+                    dst.append(float(v))
+                except ValueError:
+                    pass
             for name, v in zip(names, parts[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "mem_mhz": statistics.median(mem) if mem else None,
+                "power_w": statistics.median(pw) if pw else None}
 
 
 def aggregate(torch, dist, secs, iters, device):

@@ -164,12 +164,13 @@ int hpr_get_trace(const hpr_ctx *ctx, int64_t k, double *xbar, double *xhat, dou
                   double *ybar, double *y);
 
 /* Times `reps` plain HPR iterations (Section 3.3: the A^T phase with the x update,
- * then the A phase with the y update) of the form selected by opt.precision, launched
- * one kernel at a time, with CUDA events
- * around each kernel on the context's stream.  Starts from the current iterate and
- * advances it (call after hpr_solve).  Writes the average duration in milliseconds of
- * the x phase (ms_x), the y phase (ms_y) and of a whole iteration (ms_iter); any
- * pointer may be NULL.  HPR_ERR_STATE before the first solve. */
+ * then the A phase with the y update) of the form selected by opt.precision: reps + 2
+ * iterations are enqueued back to back on the context's stream with a CUDA event between
+ * every two kernels and one host synchronisation at the end; the first two iterations
+ * are left out of the averages.  Starts from the current iterate and advances it (call
+ * after hpr_solve).  Writes the average duration in milliseconds of the x phase (ms_x),
+ * the y phase (ms_y) and of a whole iteration (ms_iter); any pointer may be NULL.
+ * HPR_ERR_STATE before the first solve. */
 int hpr_time_iteration(hpr_ctx *ctx, int64_t reps, double *ms_x, double *ms_y, double *ms_iter);
 
 /* Allocation-free power method (the paper has no counterpart: it is an extra entry
