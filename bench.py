@@ -152,6 +152,16 @@ def read_bandwidth_probe(torch):
     return (1 << 30) / (best * 1e-3) / 1e9
 
 
+# the Section 4.2 ablation: DR, + restart & Halpern (HDR, fixed sigma), + sigma update (HDR),
+# + relaxation (HPR, the method itself)
+VARIANTS = {
+    "hpr": dict(halpern=1, reflect=1, restart=1, sigma_update=1),
+    "hdr": dict(halpern=1, reflect=0, restart=1, sigma_update=1),
+    "hdr_fixed_sigma": dict(halpern=1, reflect=0, restart=1, sigma_update=0),
+    "dr": dict(halpern=0, reflect=0, restart=0, sigma_update=0),
+}
+
+
 def workload(args):
     from paper_2408_12179_b300 import lpgen
 
@@ -163,6 +173,7 @@ def config_dict(args, lp):
                         f"Zipf(1.5) column counts, values +-10^U(-3,3), 20% free columns, seed {args.seed})",
             "scale": args.scale, "tol": args.tol,
             "precision": "fp64" if args.precision == 0 else "fp32 form, fp64 below kkt 1e-5",
+            "variant": args.variant,
             "l2": "working set per iteration larger than L2 (no flush)"}
 
 
@@ -180,7 +191,7 @@ def run_reference(args):
     it = args.sample_iters
     times = []
     for step in range(args.warmup + args.steps):
-        r = oracle.solve(lp, max_iter=it, lambda_fixed=1.0, checks_cap=16)
+        r = oracle.solve(lp, max_iter=it, lambda_fixed=1.0, checks_cap=16, **VARIANTS[args.variant])
         if step >= args.warmup:
             times.append(r["info"]["seconds"])
     tot = sum(times)
@@ -217,6 +228,7 @@ def run_ours(args):
                 precision=args.precision)
     if args.lambda_fixed > 0:
         opts["lambda_fixed"] = args.lambda_fixed   # profiling aid: skips the power method
+    opts.update(VARIANTS[args.variant])
     solver = hpr.Solver(lp, **opts)
 
     def barrier():
@@ -293,7 +305,8 @@ def run_ours(args):
         import oracle
 
         it = args.sample_iters
-        r = oracle.solve(lp, max_iter=it, lambda_fixed=infos[-1]["lambda"], checks_cap=16)
+        r = oracle.solve(lp, max_iter=it, lambda_fixed=infos[-1]["lambda"], checks_cap=16,
+                         **VARIANTS[args.variant])
         cpu = {"value": it / r["info"]["seconds"], "unit": "iter/s",
                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
                "sample": f"{it} oracle iterations (one check) of the full workload, lambda fixed to the "
@@ -350,6 +363,8 @@ def main():
                     help="0: FP64; 1: FP32 form, then FP64 below KKT 1e-5")
     ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true",
                     help="also time one plain FP64 solve and report it beside the chosen form")
+    ap.add_argument("--variant", choices=list(VARIANTS), default="hpr",
+                    help="ablation variant of Section 4.2 (default: HPR-LP itself)")
     ap.add_argument("--lambda-fixed", dest="lambda_fixed", type=float, default=0.0,
                     help="use this lambda instead of the power method (short profiling runs)")
     args = ap.parse_args()

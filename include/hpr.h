@@ -90,6 +90,12 @@ typedef struct {
                                  then FP64 iterates from the first check with
                                  kkt < switch_tol */
     double switch_tol;        /* KKT level of the switch to FP64 iterates (1e-5) */
+    int64_t halpern;          /* 1: Halpern step w = w0/(t+2) + (t+1)/(t+2) w_target of
+                                 Algorithm 2 (default); 0: w = w_target (ablation) */
+    int64_t reflect;          /* 1: w_target = w_hat = 2 w_bar - w, the relaxation step of
+                                 Algorithm 2 (default); 0: w_target = w_bar (the DR and
+                                 HDR variants of the Section 4.2 ablation).  The y step
+                                 uses A(2 x_bar - x) either way (eq. update-y-2) */
 } hpr_options;
 
 /* Result summary (original, unscaled problem). */

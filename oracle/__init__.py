@@ -49,7 +49,8 @@ class _Opts(ctypes.Structure):
                 ("pc_alpha", ctypes.c_double), ("power_max_iter", ctypes.c_int64),
                 ("power_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("lambda_fixed", ctypes.c_double), ("restart", ctypes.c_int64),
-                ("sigma_update", ctypes.c_int64), ("trace_iters", ctypes.c_int64)]
+                ("sigma_update", ctypes.c_int64), ("trace_iters", ctypes.c_int64),
+                ("halpern", ctypes.c_int64), ("reflect", ctypes.c_int64)]
 
 
 class _Out(ctypes.Structure):
@@ -61,7 +62,7 @@ class _Out(ctypes.Structure):
 DEFAULTS = dict(tol=1e-8, max_iter=100_000, check_every=150, alpha1=0.2, alpha2=0.6,
                 alpha3=0.2, sigma0=1.0, ruiz_iters=10, pc_alpha=1.0, power_max_iter=5000,
                 power_tol=1e-10, seed=0x48505221, lambda_fixed=0.0, restart=1,
-                sigma_update=1, trace_iters=0)
+                sigma_update=1, trace_iters=0, halpern=1, reflect=1)
 
 
 def lib():

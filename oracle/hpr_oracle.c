@@ -71,6 +71,8 @@ typedef struct {
     int64_t restart;         /* 0 disables the restart criteria */
     int64_t sigma_update;    /* 0 keeps sigma = sigma0 at restarts */
     int64_t trace_iters;     /* record the first trace_iters iterations */
+    int64_t halpern;         /* 0: w = w_target instead of the Halpern step (ablation) */
+    int64_t reflect;         /* 0: w_target = w_bar instead of w_hat = 2 w_bar - w (ablation) */
 } orc_opts;
 
 /* info[] layout */
@@ -450,10 +452,19 @@ int orc_hpr(const orc_lp *P, const orc_opts *O, orc_out *out)
             t = 0;
             r++;
         } else {
-            /* Halpern step of Algorithm 2: w = w0/(t+2) + (t+1)/(t+2) w_hat */
-            const double a = 1.0 / (double)(t + 2), bcoef = (double)(t + 1) / (double)(t + 2);
-            for (int64_t j = 0; j < n; ++j) x[j] = a * x0[j] + bcoef * xhat[j];
-            for (int64_t i = 0; i < m; ++i) y[i] = a * y0[i] + bcoef * yhat[i];
+            /* Halpern step of Algorithm 2: w = w0/(t+2) + (t+1)/(t+2) w_hat.  Ablation
+             * (Section 4.2): the target is w_bar instead of w_hat without the relaxation
+             * step, and w = target without the Halpern step (the DR method when both are
+             * off, with restarts and sigma updates off too) */
+            const double *tx = O->reflect ? xhat : xbar, *ty = O->reflect ? yhat : ybar;
+            if (O->halpern) {
+                const double a = 1.0 / (double)(t + 2), bcoef = (double)(t + 1) / (double)(t + 2);
+                for (int64_t j = 0; j < n; ++j) x[j] = a * x0[j] + bcoef * tx[j];
+                for (int64_t i = 0; i < m; ++i) y[i] = a * y0[i] + bcoef * ty[i];
+            } else {
+                for (int64_t j = 0; j < n; ++j) x[j] = tx[j];
+                for (int64_t i = 0; i < m; ++i) y[i] = ty[i];
+            }
             t++;
         }
 

@@ -389,7 +389,7 @@ EpiX<CHECK> epi_x(hpr_ctx *c, int it)
     e.partials = c->partials; e.pstride = c->pstride;
     e.c = c->cp; e.l = c->lp; e.u = c->up; e.x0 = c->x0;
     e.x = c->x; e.xhat = c->xhat; e.xbar = c->xbar; e.zbar = c->zbar; e.dx = c->dx;
-    e.ctl = c->ctl; e.it = it;
+    e.ctl = c->ctl; e.it = it; e.reflect = (int)c->opt.reflect;
     return e;
 }
 
@@ -401,7 +401,7 @@ EpiY<CHECK> epi_y(hpr_ctx *c, int it)
     e.q[0] = Q_DY2; e.q[1] = Q_YY0; e.q[2] = Q_BY;
     e.partials = c->partials; e.pstride = c->pstride;
     e.b = c->bp; e.y0 = c->y0; e.y = c->y; e.ybar = c->ybar; e.dy = c->dy;
-    e.ctl = c->ctl; e.it = it; e.ineq = c->ineq;
+    e.ctl = c->ctl; e.it = it; e.ineq = c->ineq; e.reflect = (int)c->opt.reflect;
     return e;
 }
 
@@ -414,7 +414,7 @@ EpiX32<CHECK> epi_x32(hpr_ctx *c, int it)
     e.partials = c->partials; e.pstride = c->pstride;
     e.c = c->cp; e.l = c->lp; e.u = c->up; e.x0 = c->x0;
     e.x = c->x32; e.xhat = c->xhat32; e.xbar = c->xbar; e.zbar = c->zbar; e.dx = c->dx;
-    e.ctl = c->ctl; e.it = it;
+    e.ctl = c->ctl; e.it = it; e.reflect = (int)c->opt.reflect;
     return e;
 }
 
@@ -426,7 +426,7 @@ EpiY32<CHECK> epi_y32(hpr_ctx *c, int it)
     e.q[0] = Q_DY2; e.q[1] = Q_YY0; e.q[2] = Q_BY;
     e.partials = c->partials; e.pstride = c->pstride;
     e.b = c->bp; e.y0 = c->y0; e.y = c->y32; e.ybar = c->ybar; e.dy = c->dy;
-    e.ctl = c->ctl; e.it = it; e.ineq = c->ineq;
+    e.ctl = c->ctl; e.it = it; e.ineq = c->ineq; e.reflect = (int)c->opt.reflect;
     return e;
 }
 
@@ -836,6 +836,8 @@ int hpr_default_options(hpr_options *o)
     o->cuda_stream = nullptr;
     o->precision = 0;
     o->switch_tol = 1e-5;
+    o->halpern = 1;
+    o->reflect = 1;
     return HPR_OK;
 }
 
@@ -852,6 +854,8 @@ static int check_options(hpr_ctx *ctx, const hpr_options *o)
     if (!(o->lambda_fixed >= 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "lambda_fixed must be >= 0");
     if (o->precision != 0 && o->precision != 1) return fail_arg(ctx, HPR_ERR_ARG, "precision must be 0 or 1");
     if (!(o->switch_tol >= 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "switch_tol must be >= 0");
+    if (o->halpern != 0 && o->halpern != 1) return fail_arg(ctx, HPR_ERR_ARG, "halpern must be 0 or 1");
+    if (o->reflect != 0 && o->reflect != 1) return fail_arg(ctx, HPR_ERR_ARG, "reflect must be 0 or 1");
     return HPR_OK;
 }
 
@@ -961,6 +965,10 @@ int hpr_set_options(hpr_ctx *ctx, const hpr_options *opt)
     if (opt->seed != ctx->opt.seed || opt->power_tol != ctx->opt.power_tol ||
         opt->power_max_iter != ctx->opt.power_max_iter)
         ctx->have_power = false;
+    if (opt->reflect != ctx->opt.reflect) {   // captured graphs hold the kernels' arguments
+        for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+        ctx->graphs.clear();
+    }
     ctx->opt = *opt;
     ctx->opt.cuda_stream = old_stream;   // the stream is fixed at creation
     ctx->opt.ruiz_iters = ruiz;
@@ -1053,8 +1061,8 @@ int hpr_solve(hpr_ctx *ctx, double tol)
         h->inv_ls = 1.0 / (lambda * sigma);
         for (int i = 0; i < L; ++i) {
             const double tt = (double)(t + i);
-            h->h[2 * i] = 1.0 / (tt + 2.0);
-            h->h[2 * i + 1] = (tt + 1.0) / (tt + 2.0);
+            h->h[2 * i] = o.halpern ? 1.0 / (tt + 2.0) : 0.0;   // 0 and 1: w = w_target exactly
+            h->h[2 * i + 1] = o.halpern ? (tt + 1.0) / (tt + 2.0) : 1.0;
         }
         CK(cudaMemcpyAsync(ctx->ctl, h, sizeof(DevCtl) + sizeof(double) * 2 * L,
                            cudaMemcpyHostToDevice, s));

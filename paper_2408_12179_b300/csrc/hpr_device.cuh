@@ -307,6 +307,7 @@ struct EpiX {
     double *x, *xhat, *xbar, *zbar, *dx;
     const DevCtl *ctl;           // sigma and the Halpern weights of iteration `it`
     int it;
+    int reflect;                 // 1: Halpern target x_hat (Algorithm 2); 0: x_bar
     double sigma, ha, hb;
     struct Pre { double x, x0, c, l, u; };
     __device__ __forceinline__ void load()
@@ -325,7 +326,7 @@ struct EpiX {
         const double v = fma(sigma, s[0] - p.c, p.x);   // x + sigma (A^T y - c)
         const double xb_ = clamp_lu(v, p.l, p.u);       // Pi_C
         const double xh = fma(2.0, xb_, -p.x);          // 2 x_bar - x
-        const double xn = fma(hb, xh, ha * p.x0);       // x0/(t+2) + (t+1)/(t+2) x_hat
+        const double xn = fma(hb, reflect ? xh : xb_, ha * p.x0);   // x0/(t+2) + (t+1)/(t+2) x_hat
         if (act) {
             xhat[j] = xh;
             x[j] = xn;
@@ -360,6 +361,7 @@ struct EpiY {
     const DevCtl *ctl;           // 1/(lambda sigma) and the Halpern weights of iteration `it`
     int it;
     const unsigned char *ineq;   // ineq[i] = 1 for the rows of A2 (renumbered order)
+    int reflect;                 // 1: Halpern target y_hat (Algorithm 2); 0: y_bar
     double inv_ls, ha, hb;
     struct Pre { double y, b, y0; unsigned char ineq; };
     __device__ __forceinline__ void load()
@@ -378,7 +380,7 @@ struct EpiY {
         double yb = fma(p.b - s[0], inv_ls, p.y);       // y + (b - A x_hat) / (lambda sigma)
         if (p.ineq) yb = pos_part(yb);                  // Pi_{R^m2_+}
         const double yh = fma(2.0, yb, -p.y);
-        const double yn = fma(hb, yh, ha * p.y0);
+        const double yn = fma(hb, reflect ? yh : yb, ha * p.y0);
         if (act) y[i] = yn;
         if (CHECK && act) {
             const double d = p.y - yb;
@@ -407,6 +409,7 @@ struct EpiX32 {
     double *xbar, *zbar, *dx;
     const DevCtl *ctl;
     int it;
+    int reflect;
     double sigma, ha, hb;
     struct Pre { double x0, c, l, u; float x; };
     __device__ __forceinline__ void load()
@@ -423,7 +426,7 @@ struct EpiX32 {
         const double v = fma(sigma, s[0] - p.c, xj);
         const double xb_ = clamp_lu(v, p.l, p.u);
         const double xh = fma(2.0, xb_, -xj);
-        const double xn = fma(hb, xh, ha * p.x0);
+        const double xn = fma(hb, reflect ? xh : xb_, ha * p.x0);
         if (act) {
             xhat[j] = (float)xh;
             x[j] = (float)xn;
@@ -458,6 +461,7 @@ struct EpiY32 {
     const DevCtl *ctl;
     int it;
     const unsigned char *ineq;
+    int reflect;
     double inv_ls, ha, hb;
     struct Pre { double b, y0; float y; unsigned char ineq; };
     __device__ __forceinline__ void load()
@@ -474,7 +478,7 @@ struct EpiY32 {
         double yb = fma(p.b - s[0], inv_ls, yi);
         if (p.ineq) yb = pos_part(yb);
         const double yh = fma(2.0, yb, -yi);
-        const double yn = fma(hb, yh, ha * p.y0);
+        const double yn = fma(hb, reflect ? yh : yb, ha * p.y0);
         if (act) y[i] = (float)yn;
         if (CHECK && act) {
             const double dd = yi - yb;

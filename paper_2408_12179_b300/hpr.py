@@ -43,7 +43,8 @@ class hpr_options(ctypes.Structure):
                 ("restart", ctypes.c_int64), ("sigma_update", ctypes.c_int64),
                 ("trace_iters", ctypes.c_int64), ("use_graph", ctypes.c_int64),
                 ("verbose", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
-                ("precision", ctypes.c_int64), ("switch_tol", ctypes.c_double)]
+                ("precision", ctypes.c_int64), ("switch_tol", ctypes.c_double),
+                ("halpern", ctypes.c_int64), ("reflect", ctypes.c_int64)]
 
 
 class hpr_info(ctypes.Structure):

@@ -425,3 +425,57 @@ def test_thread_count_does_not_change_results(tmp_path):
         subprocess.run([sys.executable, "-c", code, str(p)], check=True, env=env)
         outs.append(np.load(p))
     assert np.array_equal(outs[0], outs[1])
+
+
+# ------------------------------------------------------------------ ablation variants (Section 4.2)
+
+VARIANTS = {  # Section 4.2, Figure 1: DR -> + restart & Halpern -> + sigma update -> + relaxation
+    "DR": dict(halpern=0, reflect=0, restart=0, sigma_update=0),
+    "HDR_fixed_sigma": dict(halpern=1, reflect=0, restart=1, sigma_update=0),
+    "HDR": dict(halpern=1, reflect=0, restart=1, sigma_update=1),
+    "HPR": dict(halpern=1, reflect=1, restart=1, sigma_update=1),
+}
+
+
+@pytest.mark.parametrize("reflect", [0, 1])
+def test_dr_and_pr_fixed_point_residual_is_monotone(orc, reflect):
+    """Without the Halpern step the iteration is w^{k+1} = G(w^k) with G: w -> w_bar =
+    (M + T)^{-1} M w, the preconditioned proximal point map of the dPPM form of
+    Algorithm 1 (Proposition prop:equ-acc-PADMM-acc-dPPM), firmly nonexpansive in the
+    M-seminorm (DR, reflect 0), or its reflection 2G - I, nonexpansive (PR, reflect 1).
+    Either way ||w^{k+1} - w^k||_M cannot increase.  Checked on the trace with an M-norm
+    written here from eq. (def:M) with T1 = lambda I - A A^*, lambda >= lambda_1(A A^*)
+    from a dense eigensolver."""
+    lp = lpgen.planted_tiny(4)
+    s = _scaled(orc, lp)
+    A = s["A"]
+    lam = float(np.linalg.eigvalsh((A @ A.T).toarray())[-1]) * (1 + 1e-12)
+    N = 300
+    r = orc.solve(lp, max_iter=N, trace_iters=N, lambda_fixed=lam, restart=0, sigma_update=0,
+                  halpern=0, reflect=reflect, check_every=10 ** 9)
+    tr = r["trace"]
+    steps = []
+    for k in range(N):
+        dx = tr["x"][k] - _prev(tr, "x", k, lp.n)
+        dy = tr["y"][k] - _prev(tr, "y", k, lp.m)
+        steps.append(_M_norm(A, 1.0, lam, dy, dx))
+    assert steps[0] > 0.0
+    for k in range(1, N):
+        assert steps[k] <= steps[k - 1] * (1 + 1e-9) + 1e-15, (k, steps[k], steps[k - 1])
+    # the DR step is w_bar itself, the PR step its reflection
+    k = 57
+    target = tr["xbar"][k] if reflect == 0 else 2.0 * tr["xbar"][k] - _prev(tr, "x", k, lp.n)
+    assert np.array_equal(tr["x"][k], target)
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_ablation_variants_reach_planted_optimum(orc, variant):
+    """Each variant of the Section 4.2 ablation converges on a planted LP (the DR method,
+    Steps 1-3 of Algorithm 1 iterated, at a looser tolerance: it is the slow baseline)."""
+    lp = lpgen.planted_tiny(2)
+    tol = 1e-6 if variant == "DR" else 1e-8
+    r = orc.solve(lp, tol=tol, max_iter=400_000, **VARIANTS[variant])
+    assert r["info"]["status"] == 0, variant
+    ind = K.kkt(lp, r["x"], r["y"], r["z"])
+    assert ind["kkt"] <= tol * (1 + 1e-6)
+    assert abs(ind["pobj"] - lp.planted_objective) <= 10 * tol * (1 + abs(lp.planted_objective))
