@@ -165,12 +165,19 @@ VARIANTS = {
 def workload(args):
     from paper_2408_12179_b300 import lpgen
 
+    if args.workload == "mcf":
+        return lpgen.mcf_lp(args.seed, nodes=max(2, int(round(1_000_000 * args.scale))))
     return lpgen.planted_medium(args.seed, args.scale)
 
 
 def config_dict(args, lp):
-    return {"workload": f"medium sparse planted LP (m={lp.m}, m1={lp.m1}, n={lp.n}, nnz={lp.nnz}, "
-                        f"Zipf(1.5) column counts, values +-10^U(-3,3), 20% free columns, seed {args.seed})",
+    if args.workload == "mcf":
+        name = (f"min-cost multicommodity flow LP (random geometric 8-NN digraph, 4 commodities; "
+                f"m={lp.m}, m1={lp.m1}, n={lp.n}, nnz={lp.nnz}, seed {args.seed})")
+    else:
+        name = (f"medium sparse planted LP (m={lp.m}, m1={lp.m1}, n={lp.n}, nnz={lp.nnz}, "
+                f"Zipf(1.5) column counts, values +-10^U(-3,3), 20% free columns, seed {args.seed})")
+    return {"workload": name,
             "scale": args.scale, "tol": args.tol,
             "precision": "fp64" if args.precision == 0 else "fp32 form, fp64 below kkt 1e-5",
             "variant": args.variant,
@@ -363,6 +370,9 @@ def main():
                     help="0: FP64; 1: FP32 form, then FP64 below KKT 1e-5")
     ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true",
                     help="also time one plain FP64 solve and report it beside the chosen form")
+    ap.add_argument("--workload", choices=["medium", "mcf"], default="medium",
+                    help="medium sparse planted LP (default) or the min-cost multicommodity flow LP "
+                         "(1M nodes at scale 1)")
     ap.add_argument("--variant", choices=list(VARIANTS), default="hpr",
                     help="ablation variant of Section 4.2 (default: HPR-LP itself)")
     ap.add_argument("--lambda-fixed", dest="lambda_fixed", type=float, default=0.0,

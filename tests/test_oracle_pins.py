@@ -479,3 +479,24 @@ def test_ablation_variants_reach_planted_optimum(orc, variant):
     ind = K.kkt(lp, r["x"], r["y"], r["z"])
     assert ind["kkt"] <= tol * (1 + 1e-6)
     assert abs(ind["pobj"] - lp.planted_objective) <= 10 * tol * (1 + abs(lp.planted_objective))
+
+
+# ------------------------------------------------------------------ min-cost multicommodity flow
+
+def test_mcf_small_vs_highs(orc):
+    """The min-cost multicommodity-flow family (random geometric k-NN digraph, shared
+    capacities): no planted optimum, so the oracle's objective is pinned to HiGHS and its
+    returned point to the independent KKT evaluator."""
+    lp = lpgen.mcf_lp(0, nodes=300)
+    r = orc.solve(lp, tol=1e-8, max_iter=200_000)
+    assert r["info"]["status"] == 0
+    ind = K.kkt(lp, r["x"], r["y"], r["z"])
+    assert ind["kkt"] <= 1e-8 * (1 + 1e-6)
+    def csr32(M, sign=1.0):   # HiGHS' sparse input wants 32-bit row pointers
+        return sp.csr_matrix((sign * M.data, M.indices.astype(np.int32), M.indptr.astype(np.int32)),
+                             shape=M.shape)
+
+    res = linprog(lp.c, A_eq=csr32(lp.A1), b_eq=lp.b1, A_ub=csr32(lp.A2, -1.0), b_ub=-lp.b2,
+                  bounds=[(0, None)] * lp.n, method="highs")
+    assert res.status == 0
+    assert abs(ind["pobj"] - res.fun) <= 1e-7 * abs(res.fun)
