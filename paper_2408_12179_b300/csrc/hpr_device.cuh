@@ -252,11 +252,34 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
                 b1.add(v[3], g1[3]);
             }
         }
-        for (; k < steps; ++k) {
-            const V v = __ldcs(pv + k * 32);
-            const int c = __ldcs(pc + k * 32);
-            a0.add(v, __ldg(ee.xa + c));
-            if (NV == 2) b0.add(v, __ldg(ee.xb + c));
+        if (steps < 4) {                          // a short slice: its 1-3 steps as one batch
+            const int rem = steps;                // warp-uniform
+            V v[3], g0[3], g1[3];
+            int c[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                v[u] = u < rem ? __ldcs(pv + (k + u) * 32) : V(0);
+                c[u] = u < rem ? __ldcs(pc + (k + u) * 32) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                g0[u] = u < rem ? __ldg(ee.xa + c[u]) : V(0);
+                if (NV == 2) g1[u] = u < rem ? __ldg(ee.xb + c[u]) : V(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {         // same order as step by step
+                if (u < rem) {
+                    a0.add(v[u], g0[u]);
+                    if (NV == 2) b0.add(v[u], g1[u]);
+                }
+            }
+        } else {
+            for (; k < steps; ++k) {
+                const V v = __ldcs(pv + k * 32);
+                const int c = __ldcs(pc + k * 32);
+                a0.add(v, __ldg(ee.xa + c));
+                if (NV == 2) b0.add(v, __ldg(ee.xb + c));
+            }
         }
         if (steps >= 4) {                         // warp-uniform
             a0.merge(a1);
