@@ -215,6 +215,111 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Batched workload: `count` uneven planted LPs solved together through hpr_batch_*
+    (fused launches), one context per LP.  Warm-up solves are capped at two check
+    periods (graph capture, power method); the timed solve runs every LP to tol or the
+    iteration cap.  Also times a sample of the LPs solved one by one and as a batch of
+    their own (same instances, same options)."""
+    import torch
+
+    from paper_2408_12179_b300 import hpr, lpgen
+
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    hpr.load()
+    m_hi = max(600, int(round(50_000 * args.scale)))
+    lps = lpgen.batch_family(args.seed + rank, args.count, 500, m_hi)
+    stream = torch.cuda.Stream()
+    opts = dict(tol=args.tol, precision=args.precision, **VARIANTS[args.variant])
+    solvers = [hpr.Solver(lp, max_iter=args.max_iter, **opts) for lp in lps]
+    batch = hpr.Batch(solvers, stream.cuda_stream)
+    for s_ in solvers:
+        s_.set_options(max_iter=300)
+    for _ in range(args.warmup):
+        batch.solve(args.tol)
+    for s_ in solvers:
+        s_.set_options(max_iter=args.max_iter)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    status, res = batch.solve(args.tol)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    clocks = sampler.stop()
+    st = batch.stats()
+    batch.close()
+    conv = [r for r in res if r["status"] == hpr.HPR_OK]
+    iters = sum(int(r["info"]["iters"]) for r in res)
+    # the sample: one by one, then as a batch of its own
+    k = min(args.solo_sample, len(solvers))
+    t1 = time.perf_counter()
+    solo_iters = 0
+    for s_ in solvers[:k]:
+        solo_iters += int(s_.solve(args.tol)["info"]["iters"])
+    torch.cuda.synchronize()
+    solo_secs = time.perf_counter() - t1
+    with hpr.Batch(solvers[:k], stream.cuda_stream) as b2:
+        b2.solve(args.tol)
+        t2 = time.perf_counter()
+        b2.solve(args.tol)
+        torch.cuda.synchronize()
+        sample_batch_secs = time.perf_counter() - t2
+    for s_ in solvers:
+        s_.close()
+    if rank != 0:
+        return
+    nnz = sum(lp.nnz for lp in lps)
+    line = {
+        "metric": "LPs solved to KKT<=tol per second (batched); HPR iterations/s summed over LPs",
+        "value": len(conv) / secs, "unit": "LP/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == 0 else "f32+f64", "data": "synthetic",
+        "config": {"workload": f"batch of {len(lps)} uneven planted LPs (m log-uniform in [500, {m_hi}], "
+                               f"n = 2.5 m, density log-uniform in [0.1%, 1%], medium-LP value rules; "
+                               f"total nnz {nnz}, seed {args.seed})",
+                   "tol": args.tol, "max_iter": args.max_iter, "variant": args.variant},
+        "batch_status": hpr.hpr_status_str(int(status)), "converged": len(conv), "count": len(lps),
+        "time_to_all_s": secs, "iters_summed": iters, "iters_per_s_summed": iters / secs,
+        "periods": st["periods"], "gpu_launches": int(st["fused_launches"] + sum(int(r["info"]["launches"]) for r in res)),
+        "sample": {"lps": k, "one_by_one_s": solo_secs, "as_batch_s": sample_batch_secs,
+                   "speedup": solo_secs / sample_batch_secs, "iters": solo_iters},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_batch(args):
+    """The oracle on a bounded sample of the batch workload: `sample_iters` iterations of
+    each of the first `solo_sample` LPs, reported as HPR iterations/s summed over LPs."""
+    import oracle
+    from paper_2408_12179_b300 import lpgen
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    m_hi = max(600, int(round(50_000 * args.scale)))
+    lps = lpgen.batch_family(args.seed, args.count, 500, m_hi)[:args.solo_sample]
+    oracle.lib()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    secs = 0.0
+    its = 0
+    for lp in lps:
+        r = oracle.solve(lp, max_iter=args.sample_iters, lambda_fixed=1.0, checks_cap=16, **VARIANTS[args.variant])
+        secs += r["info"]["seconds"]
+        its += args.sample_iters
+    value = its / secs
+    line = {"impl": "reference", "metric": "HPR iterations/s summed over LPs (batch workload sample)",
+            "value": value, "unit": "iter/s", "n_gpus": args.gpus, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * secs, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"first {len(lps)} LPs of the batch workload", "tol": args.tol},
+            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.sample_iters} oracle iterations of each of {len(lps)} LPs"},
+            "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -370,15 +475,23 @@ def main():
                     help="0: FP64; 1: FP32 form, then FP64 below KKT 1e-5")
     ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true",
                     help="also time one plain FP64 solve and report it beside the chosen form")
-    ap.add_argument("--workload", choices=["medium", "mcf"], default="medium",
-                    help="medium sparse planted LP (default) or the min-cost multicommodity flow LP "
-                         "(1M nodes at scale 1)")
+    ap.add_argument("--workload", choices=["medium", "mcf", "batch"], default="medium",
+                    help="medium sparse planted LP (default), the min-cost multicommodity flow LP "
+                         "(1M nodes at scale 1), or a batch of uneven planted LPs solved in one "
+                         "batched run (m log-uniform in [500, 50000 * scale])")
+    ap.add_argument("--count", type=int, default=512, help="LPs in the batch workload")
+    ap.add_argument("--solo-sample", dest="solo_sample", type=int, default=16,
+                    help="batch workload: LPs also solved one by one, and as a batch of their own")
     ap.add_argument("--variant", choices=list(VARIANTS), default="hpr",
                     help="ablation variant of Section 4.2 (default: HPR-LP itself)")
     ap.add_argument("--lambda-fixed", dest="lambda_fixed", type=float, default=0.0,
                     help="use this lambda instead of the power method (short profiling runs)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.impl == "reference" and args.workload == "batch":
+        run_reference_batch(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -207,6 +207,32 @@ int hpr_power_noalloc(int64_t m, int64_t n, const int32_t *A_row_ptr, const int3
                       const double *At_val, uint64_t seed, int64_t max_iter, double tol,
                       double *u, double *s, void *cuda_stream, double *lambda, int64_t *iters);
 
+/* ---- Batched solve (no counterpart in the paper: many independent LPs in lock step).
+ * A batch takes `count` contexts made by hpr_create (their LPs may differ in size and
+ * structure) and solves them together: each check period's normal iterations of all
+ * contexts run as fused sliced-ELL launches over one work list of every context's work
+ * units (captured as one CUDA graph per period length), while each context keeps its
+ * own power method (run on up to 8 host worker threads with their own streams), checks,
+ * restart / sigma decisions (Algorithm 2 and 3), FP32 -> FP64 switch and termination.
+ * Results are read per context with hpr_get.  Each context's options are those set when
+ * hpr_batch_solve is called (reflect: when the batch was created); all contexts need the
+ * same check_every and trace_iters = 0.
+ *   ctxs         `count` distinct contexts on the same device, none in another batch;
+ *                the batch does not own them: destroy the batch first, then the
+ *                contexts.  While in the batch a context cannot be solved on its own
+ *                (hpr_solve returns HPR_ERR_STATE) and runs on the batch's stream.
+ *   cuda_stream  the batch's stream (NULL: a stream of its own).
+ * hpr_batch_solve returns HPR_OK when every context converged, else the status of a
+ * context that did not (HPR_MAX_ITER / HPR_TIME_LIMIT), or an error code; detail in
+ * hpr_last_error(NULL) or of the context. */
+typedef struct hpr_batch hpr_batch;
+int hpr_batch_create(hpr_batch **out, int64_t count, hpr_ctx *const *ctxs, void *cuda_stream);
+int hpr_batch_solve(hpr_batch *batch, double tol);
+/* Wall time of the last hpr_batch_solve (power methods included), its check periods and
+ * the fused launches it made; any pointer may be NULL. */
+int hpr_batch_stats(const hpr_batch *batch, double *solve_time_s, int64_t *periods, int64_t *fused_launches);
+void hpr_batch_destroy(hpr_batch *batch);
+
 /* Detail of the last error of ctx (a static string when ctx is NULL). */
 const char *hpr_last_error(const hpr_ctx *ctx);
 

@@ -26,6 +26,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <thread>
+#include <type_traits>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -57,15 +59,32 @@ struct SellDev {
     int grid = 0;                 // CTAs of a sliced-ELL launch: ceil(nruns / warps per CTA)
     int *srow = nullptr, *sptr = nullptr, *wstart = nullptr, *col = nullptr;
     unsigned char *slg = nullptr;
+    std::vector<float> ucost;     // host: cost of each work unit (for batched work lists)
     double *val = nullptr;
     float *val32 = nullptr;       // FP32 copy of val (the FP32 form)
     int *src = nullptr;           // CSR position of each stored entry (-1: padding)
+};
+
+// state of a solve between its periods (Algorithm 2's counters and the last check)
+struct SolveState {
+    double tol = 1e-8, t0 = 0.0, lambda = 0.0, sigma = 1.0;
+    int64_t k = 0, t = 0, r = 0;          // total, inner and outer counters
+    int status = HPR_MAX_ITER;
+    double R0 = 0.0, Rprev = 0.0;
+    double last_pobj = 0, last_dobj = 0, last_ep = 0, last_ed = 0, last_gap = 0, last_kkt = 0;
+    double time_1e4 = -1.0;
+    int64_t iters_1e4 = -1, iters_fp32 = 0;
+    bool tracing = false, done = false;
+    bool ctl_off = false;                 // batched: the control block already says inactive
+    int L = 0;                            // the current period: iterations and whether it
+    bool first_r0 = false;                // starts an inner loop (t = 0)
 };
 
 struct hpr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t home_stream = nullptr;   // the context's own stream (a batch swaps `stream`)
     hpr_options opt{};
     int64_t m1 = 0, m2 = 0, m = 0, n = 0, nnz = 0;
     double norm_b = 0.0, norm_c = 0.0, beta_b = 1.0, beta_c = 1.0;
@@ -122,6 +141,8 @@ struct hpr_ctx {
     int64_t power_iters = 0;
     double power_time = 0.0;
     hpr_info info{};
+    SolveState ss;
+    bool batched = false;         // owned by a batch: solved only through hpr_batch_solve
     std::vector<hpr_check_record> checks;
     std::string err;
 };
@@ -212,6 +233,7 @@ struct SellHost {
     int nslices = 0;
     std::vector<int> srow, sptr, col, src, wstart;
     std::vector<unsigned char> slg;
+    std::vector<float> ucost;        // cost of each work unit (steps + epilogue share)
 };
 
 SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int rows,
@@ -259,8 +281,12 @@ SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int 
         for (int sl = gfirst[g]; sl < gfirst[g + 1]; ++sl) gc += scost[(size_t)sl];
         if (gc <= UNIT_COST) {
             h.wstart.push_back(gfirst[g]);
+            h.ucost.push_back((float)gc);
         } else {
-            for (int sl = gfirst[g]; sl < gfirst[g + 1]; ++sl) h.wstart.push_back(sl);
+            for (int sl = gfirst[g]; sl < gfirst[g + 1]; ++sl) {
+                h.wstart.push_back(sl);
+                h.ucost.push_back((float)scost[(size_t)sl]);
+            }
         }
     }
     h.wstart.push_back(h.nslices);
@@ -320,7 +346,7 @@ void free_all(hpr_ctx *c)
     if (c->scal_h) cudaFreeHost(c->scal_h);
     if (c->ctl_h) cudaFreeHost(c->ctl_h);
     if (c->pctl_h) cudaFreeHost(c->pctl_h);
-    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->own_stream && c->home_stream) cudaStreamDestroy(c->home_stream);
 }
 
 double now_s()
@@ -682,6 +708,7 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     auto upload_sell = [&](SellDev &D, const SellHost &H, int rows) -> int {
         D.rows = rows; D.nslices = H.nslices;
         D.nruns = (int)H.wstart.size() - 1;
+        D.ucost = H.ucost;
         D.grid = std::max(1, (D.nruns + TB / 32 - 1) / (TB / 32));
         D.entries = (int64_t)H.col.size();
         DALLOC(D.val32, D.entries);
@@ -948,6 +975,7 @@ int hpr_create(hpr_ctx **out, const hpr_csr *A1, const hpr_csr *A2, const double
         if (e != cudaSuccess) return bail(fail_cuda(ctx, e, "cudaStreamCreate", __LINE__));
         ctx->own_stream = true;
     }
+    ctx->home_stream = ctx->stream;
     st = upload_and_prepare(ctx, A1, A2, b1, b2, c, l, u);
     if (st) return bail(st);
     *out = ctx;
@@ -988,11 +1016,20 @@ int hpr_power(hpr_ctx *ctx, double *lambda, int64_t *iters)
     return HPR_OK;
 }
 
-int hpr_solve(hpr_ctx *ctx, double tol)
+}  // extern "C"
+
+namespace {
+
+// ---------------------------------------------------------------- solve, in stages
+// A solve is: solve_begin (power method, origin start), then periods of up to
+// check_every iterations ending with a check -- period_prepare (control block of the
+// period), the period's kernels, period_readback (check scalars to the host), one
+// synchronisation, period_after (termination, restart and sigma decisions of the check)
+// -- and solve_finish (back-map, summary).  hpr_solve runs one context through them;
+// hpr_batch_solve runs many in lock step with fused kernels.
+
+int solve_begin(hpr_ctx *ctx, double tol)
 {
-    if (!ctx) return HPR_ERR_ARG;
-    if (!(tol > 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "tol must be > 0");
-    cudaSetDevice(ctx->device);
     hpr_options &o = ctx->opt;
     const int64_t n = ctx->n, m = ctx->m;
     cudaStream_t s = ctx->stream;
@@ -1016,7 +1053,10 @@ int hpr_solve(hpr_ctx *ctx, double tol)
     if (st) return st;
 
     CK(cudaStreamSynchronize(s));
-    const double t0 = now_s();
+    SolveState &S = ctx->ss;
+    S = SolveState{};
+    S.tol = tol;
+    S.t0 = now_s();
     ctx->launches = 0;
 
     // ---- T1 = lambda I - A A^*: power method (counted in the solve time, Section 4.1)
@@ -1027,9 +1067,9 @@ int hpr_solve(hpr_ctx *ctx, double tol)
     } else {
         st = run_power(ctx);
         if (st) return st;
-        ctx->power_time = now_s() - t0;
+        ctx->power_time = now_s() - S.t0;
     }
-    const double lambda = ctx->lambda;
+    S.lambda = ctx->lambda;
 
     // ---- origin start, sigma_0 (Section 4.1)
     CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * n, s));
@@ -1039,208 +1079,273 @@ int hpr_solve(hpr_ctx *ctx, double tol)
     CK(cudaMemsetAsync(ctx->x32, 0, sizeof(float) * n, s));
     CK(cudaMemsetAsync(ctx->y32, 0, sizeof(float) * m, s));
     ctx->form = (int)o.precision;
-    int64_t iters_fp32 = 0;
+    S.sigma = o.sigma0;
+    S.status = HPR_MAX_ITER;
+    S.tracing = ctx->trace_n > 0;
+    S.done = o.max_iter <= 0;
+    return HPR_OK;
+}
 
-    double sigma = o.sigma0;
-    int64_t k = 0, t = 0, r = 0;
-    int status = HPR_MAX_ITER;
-    double R0 = 0.0, Rprev = 0.0;
-    double last_pobj = 0, last_dobj = 0, last_ep = 0, last_ed = 0, last_gap = 0, last_kkt = 0;
-    double time_1e4 = -1.0;
-    int64_t iters_1e4 = -1;
-    const bool tracing = ctx->trace_n > 0;
+// control block of the next period: sigma, 1/(lambda sigma) and the Halpern weights of
+// its L iterations; fused_lo / fused_hi: the iterations that fused launches may run
+int period_prepare(hpr_ctx *ctx)
+{
+    SolveState &S = ctx->ss;
+    const hpr_options &o = ctx->opt;
+    const int64_t to_check = o.check_every - (S.k % o.check_every);
+    S.L = (int)std::min<int64_t>(to_check, o.max_iter - S.k);
+    S.first_r0 = (S.t == 0);
+    DevCtl *h = ctx->ctl_h;
+    h->sigma = S.sigma;
+    h->inv_ls = 1.0 / (S.lambda * S.sigma);
+    h->fused_lo = S.first_r0 ? 1 : 0;
+    h->fused_hi = S.L - 1;
+    h->form = ctx->form;
+    h->active = S.done ? 0 : 1;
+    for (int i = 0; i < S.L; ++i) {
+        const double tt = (double)(S.t + i);
+        h->h[2 * i] = o.halpern ? 1.0 / (tt + 2.0) : 0.0;   // 0 and 1: w = w_target exactly
+        h->h[2 * i + 1] = o.halpern ? (tt + 1.0) / (tt + 2.0) : 1.0;
+    }
+    CK(cudaMemcpyAsync(ctx->ctl, h, sizeof(DevCtl) + sizeof(double) * 2 * S.L, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    return HPR_OK;
+}
 
-    while (k < o.max_iter) {
-        // iterations up to and including the next check
-        const int64_t to_check = o.check_every - (k % o.check_every);
-        const int L = (int)std::min<int64_t>(to_check, o.max_iter - k);
-        const bool first_r0 = (t == 0);
-
-        DevCtl *h = ctx->ctl_h;
-        h->sigma = sigma;
-        h->inv_ls = 1.0 / (lambda * sigma);
+// the period's kernels of a context run on its own (trace mode, a captured graph, or
+// direct launches)
+int period_enqueue_own(hpr_ctx *ctx)
+{
+    SolveState &S = ctx->ss;
+    const hpr_options &o = ctx->opt;
+    cudaStream_t s = ctx->stream;
+    const int L = S.L;
+    const bool first_r0 = S.first_r0;
+    int st;
+    const bool trace_period = S.tracing && S.k < ctx->trace_n;
+    if (trace_period) {
         for (int i = 0; i < L; ++i) {
-            const double tt = (double)(t + i);
-            h->h[2 * i] = o.halpern ? 1.0 / (tt + 2.0) : 0.0;   // 0 and 1: w = w_target exactly
-            h->h[2 * i + 1] = o.halpern ? (tt + 1.0) / (tt + 2.0) : 1.0;
-        }
-        CK(cudaMemcpyAsync(ctx->ctl, h, sizeof(DevCtl) + sizeof(double) * 2 * L,
-                           cudaMemcpyHostToDevice, s));
-
-        const bool trace_period = tracing && k < ctx->trace_n;
-        if (trace_period) {
-            for (int i = 0; i < L; ++i) {
-                const bool last = (i == L - 1);
-                const bool r0 = (i == 0 && first_r0);
-                // every traced iteration stores x_bar, y_bar; checks also reduce
-                st = enqueue_iteration(ctx, i, true, last || r0, last ? 1 : 0);
+            const bool last = (i == L - 1);
+            const bool r0 = (i == 0 && first_r0);
+            // every traced iteration stores x_bar, y_bar; checks also reduce
+            st = enqueue_iteration(ctx, i, true, last || r0, last ? 1 : 0);
+            if (st) return st;
+            if (!last) {
+                st = trace_copy(ctx, S.k + i);
                 if (st) return st;
-                if (!last) {
-                    st = trace_copy(ctx, k + i);
-                    if (st) return st;
-                }
             }
-        } else if (o.use_graph) {
-            const GraphKey key{L, first_r0 ? 1 : 0, ctx->form};
-            auto itg = ctx->graphs.find(key);
-            if (itg == ctx->graphs.end()) {
-                CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                const int64_t before = ctx->launches;
-                int rr = enqueue_period(ctx, L, first_r0);
-                ctx->graph_launches[key] = ctx->launches - before;
-                ctx->launches = before;
-                cudaGraph_t g = nullptr;
-                cudaError_t e = cudaStreamEndCapture(s, &g);
-                if (rr) { if (g) cudaGraphDestroy(g); return rr; }
-                if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaStreamEndCapture", __LINE__);
-                cudaGraphExec_t ex = nullptr;
-                e = cudaGraphInstantiate(&ex, g, 0);
-                cudaGraphDestroy(g);
-                if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaGraphInstantiate", __LINE__);
-                itg = ctx->graphs.emplace(key, ex).first;
-            }
-            CK(cudaGraphLaunch(itg->second, s));
-            ctx->launches += ctx->graph_launches[key];
-        } else {
-            st = enqueue_period(ctx, L, first_r0);
-            if (st) return st;
         }
-        CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double) * 2 * NQ, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        const double elapsed = now_s() - t0;
+    } else if (o.use_graph) {
+        const GraphKey key{L, first_r0 ? 1 : 0, ctx->form};
+        auto itg = ctx->graphs.find(key);
+        if (itg == ctx->graphs.end()) {
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const int64_t before = ctx->launches;
+            int rr = enqueue_period(ctx, L, first_r0);
+            ctx->graph_launches[key] = ctx->launches - before;
+            ctx->launches = before;
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (rr) { if (g) cudaGraphDestroy(g); return rr; }
+            if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaStreamEndCapture", __LINE__);
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaGraphInstantiate", __LINE__);
+            itg = ctx->graphs.emplace(key, ex).first;
+        }
+        CK(cudaGraphLaunch(itg->second, s));
+        ctx->launches += ctx->graph_launches[key];
+    } else {
+        st = enqueue_period(ctx, L, first_r0);
+        if (st) return st;
+    }
+    return HPR_OK;
+}
 
-        const double *S1 = ctx->scal_h + NQ;
-        const double *S0 = (first_r0 && L > 1) ? ctx->scal_h : S1;
-        const int64_t kk = k + L - 1;           // index of the check iteration
-        const int64_t tl = t + L - 1;           // its inner counter
-        if (first_r0 && L > 1) {
-            R0 = merit_from(S0, sigma, lambda);
-            Rprev = R0;
-            hpr_check_record rec{};
-            rec.k = k; rec.r = r; rec.t = 0; rec.kind = 2; rec.cause = 0;
-            rec.sigma = sigma; rec.Rt = R0; rec.R0 = R0; rec.sigma_next = sigma;
-            rec.elapsed_s = elapsed;
-            ctx->checks.push_back(rec);
-        }
-        const bool is_r0 = (tl == 0);
-        const double Rt = merit_from(S1, sigma, lambda);
-        if (is_r0) {
-            R0 = Rt;
-            Rprev = Rt;
-        }
-        // termination test of Section 4.1 in the original space
-        const double bb = ctx->beta_b * ctx->beta_c;
-        const double errp = std::sqrt(S1[Q_RP]) / (1.0 + ctx->norm_b);
-        const double errd = std::sqrt(S1[Q_RD]) / (1.0 + ctx->norm_c);
-        const double pobj = bb * S1[Q_CX];
-        const double dobj = bb * (S1[Q_BY] + S1[Q_BND]);
-        const double gap = std::fabs(dobj - pobj) / (1.0 + std::fabs(pobj) + std::fabs(dobj));
-        const double kkt = std::max(errp, std::max(errd, gap));
-        last_pobj = pobj; last_dobj = dobj; last_ep = errp; last_ed = errd; last_gap = gap; last_kkt = kkt;
-        if (!std::isfinite(kkt) || !std::isfinite(Rt))
-            return fail_arg(ctx, HPR_ERR_NUMERIC, "non-finite residual at iteration " + std::to_string(kk));
-        if (time_1e4 < 0.0 && kkt <= 1e-4) {
-            time_1e4 = elapsed;
-            iters_1e4 = kk + 1;
-        }
+int period_readback(hpr_ctx *ctx)
+{
+    CK(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(double) * 2 * NQ, cudaMemcpyDeviceToHost, ctx->stream));
+    return HPR_OK;
+}
 
-        int cause = 0;
-        bool restart = false, stop = false;
-        double sigma_next = sigma, Dx = 0.0, Dy = 0.0;
-        if (kkt <= tol) {
-            stop = true;
-            status = HPR_OK;
-            cause = -1;
-        } else if (kk + 1 < o.max_iter && o.restart && !is_r0) {
-            // restart criteria eq. (restart_1)-(restart_3)
-            if (Rt <= o.alpha1 * R0) cause = 1;
-            else if (Rt <= o.alpha2 * R0 && Rt > Rprev) cause = 2;
-            else if ((double)(tl + 1) >= o.alpha3 * (double)(kk + 1)) cause = 3;
-            Rprev = Rt;
-            restart = cause != 0;
-        }
-        if (restart) {
-            // Algorithm 3 with eq. (sigma_T1!=0)
-            Dx = std::sqrt(S1[Q_XX0]);
-            Dy = std::sqrt(lambda) * std::sqrt(S1[Q_YY0]);
-            const double ratio = errd / errp;
-            if (o.sigma_update && Dx > 1e-16 && Dx < 1e12 && Dy > 1e-16 && Dy < 1e12 &&
-                errp > 0.0 && ratio > 1e-8 && ratio < 1e8)
-                sigma_next = Dx / Dy;
-            else
-                sigma_next = o.sigma_update ? 1.0 : sigma;
-        }
-        {
-            hpr_check_record rec{};
-            rec.k = kk; rec.r = r; rec.t = tl; rec.kind = 1 + (is_r0 ? 2 : 0); rec.cause = cause;
-            rec.sigma = sigma; rec.err_p = errp; rec.err_d = errd; rec.err_gap = gap; rec.kkt = kkt;
-            rec.pobj = pobj; rec.dobj = dobj; rec.Rt = Rt; rec.R0 = R0; rec.sigma_next = sigma_next;
-            rec.Dx = Dx; rec.Dy = Dy; rec.elapsed_s = elapsed;
-            ctx->checks.push_back(rec);
-        }
-        if (o.verbose)
-            fprintf(stderr, "hpr k=%lld r=%lld t=%lld sigma=%.3e kkt=%.3e (p %.2e d %.2e g %.2e) R=%.3e cause=%d %.3fs\n",
-                    (long long)(kk + 1), (long long)r, (long long)tl, sigma, kkt, errp, errd, gap, Rt,
-                    cause, elapsed);
+// after the period's synchronisation: the check of its last iteration (termination test,
+// restart criteria, SigmaUpdate, the FP32 -> FP64 switch) and the restart kernels
+int period_after(hpr_ctx *ctx, double elapsed)
+{
+    SolveState &S = ctx->ss;
+    const hpr_options &o = ctx->opt;
+    const int64_t n = ctx->n, m = ctx->m;
+    cudaStream_t s = ctx->stream;
+    const double lambda = S.lambda;
+    const int L = S.L;
+    const bool first_r0 = S.first_r0;
+    int st;
 
-        if (ctx->form == 1) iters_fp32 = kk + 1;
-        // the FP32 form hands over to FP64 iterates at the first check below switch_tol
-        const bool widen = ctx->form == 1 && !stop && kkt < o.switch_tol;
-        if (widen) ctx->form = 0;
-        if (restart && ctx->form == 1) {
-            k_restart32<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->xbar, ctx->ybar, ctx->x32,
-                                                        ctx->x0, ctx->y32, ctx->y0);
-            CKL();
-            ctx->launches += 1;
-        } else if (restart) {
-            k_restart<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->xbar, ctx->ybar, ctx->x,
-                                                      ctx->x0, ctx->y, ctx->y0);
-            CKL();
-            ctx->launches += 1;
-        } else if (widen) {
-            k_widen<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->x32, ctx->y32, ctx->x, ctx->y);
-            CKL();
-            ctx->launches += 1;
-        }
-        if (restart) {
-            sigma = sigma_next;
-            t = 0;
-            r++;
-        } else {
-            t = tl + 1;
-        }
-        if (tracing && kk < ctx->trace_n) {
-            st = trace_copy(ctx, kk);
-            if (st) return st;
-        }
-        k = kk + 1;
-        if (stop) break;
-        if (o.time_limit_s > 0.0 && elapsed >= o.time_limit_s && k < o.max_iter) {
-            status = HPR_TIME_LIMIT;
-            break;
-        }
+    const double *S1 = ctx->scal_h + NQ;
+    const double *S0 = (first_r0 && L > 1) ? ctx->scal_h : S1;
+    const int64_t kk = S.k + L - 1;           // index of the check iteration
+    const int64_t tl = S.t + L - 1;           // its inner counter
+    if (first_r0 && L > 1) {
+        S.R0 = merit_from(S0, S.sigma, lambda);
+        S.Rprev = S.R0;
+        hpr_check_record rec{};
+        rec.k = S.k; rec.r = S.r; rec.t = 0; rec.kind = 2; rec.cause = 0;
+        rec.sigma = S.sigma; rec.Rt = S.R0; rec.R0 = S.R0; rec.sigma_next = S.sigma;
+        rec.elapsed_s = elapsed;
+        ctx->checks.push_back(rec);
+    }
+    const bool is_r0 = (tl == 0);
+    const double Rt = merit_from(S1, S.sigma, lambda);
+    if (is_r0) {
+        S.R0 = Rt;
+        S.Rprev = Rt;
+    }
+    // termination test of Section 4.1 in the original space
+    const double bb = ctx->beta_b * ctx->beta_c;
+    const double errp = std::sqrt(S1[Q_RP]) / (1.0 + ctx->norm_b);
+    const double errd = std::sqrt(S1[Q_RD]) / (1.0 + ctx->norm_c);
+    const double pobj = bb * S1[Q_CX];
+    const double dobj = bb * (S1[Q_BY] + S1[Q_BND]);
+    const double gap = std::fabs(dobj - pobj) / (1.0 + std::fabs(pobj) + std::fabs(dobj));
+    const double kkt = std::max(errp, std::max(errd, gap));
+    S.last_pobj = pobj; S.last_dobj = dobj; S.last_ep = errp; S.last_ed = errd; S.last_gap = gap; S.last_kkt = kkt;
+    if (!std::isfinite(kkt) || !std::isfinite(Rt))
+        return fail_arg(ctx, HPR_ERR_NUMERIC, "non-finite residual at iteration " + std::to_string(kk));
+    if (S.time_1e4 < 0.0 && kkt <= 1e-4) {
+        S.time_1e4 = elapsed;
+        S.iters_1e4 = kk + 1;
     }
 
-    // output: the last w_bar mapped back to the original LP
+    int cause = 0;
+    bool restart = false, stop = false;
+    double sigma_next = S.sigma, Dx = 0.0, Dy = 0.0;
+    if (kkt <= S.tol) {
+        stop = true;
+        S.status = HPR_OK;
+        cause = -1;
+    } else if (kk + 1 < o.max_iter && o.restart && !is_r0) {
+        // restart criteria eq. (restart_1)-(restart_3)
+        if (Rt <= o.alpha1 * S.R0) cause = 1;
+        else if (Rt <= o.alpha2 * S.R0 && Rt > S.Rprev) cause = 2;
+        else if ((double)(tl + 1) >= o.alpha3 * (double)(kk + 1)) cause = 3;
+        S.Rprev = Rt;
+        restart = cause != 0;
+    }
+    if (restart) {
+        // Algorithm 3 with eq. (sigma_T1!=0)
+        Dx = std::sqrt(S1[Q_XX0]);
+        Dy = std::sqrt(lambda) * std::sqrt(S1[Q_YY0]);
+        const double ratio = errd / errp;
+        if (o.sigma_update && Dx > 1e-16 && Dx < 1e12 && Dy > 1e-16 && Dy < 1e12 &&
+            errp > 0.0 && ratio > 1e-8 && ratio < 1e8)
+            sigma_next = Dx / Dy;
+        else
+            sigma_next = o.sigma_update ? 1.0 : S.sigma;
+    }
+    {
+        hpr_check_record rec{};
+        rec.k = kk; rec.r = S.r; rec.t = tl; rec.kind = 1 + (is_r0 ? 2 : 0); rec.cause = cause;
+        rec.sigma = S.sigma; rec.err_p = errp; rec.err_d = errd; rec.err_gap = gap; rec.kkt = kkt;
+        rec.pobj = pobj; rec.dobj = dobj; rec.Rt = Rt; rec.R0 = S.R0; rec.sigma_next = sigma_next;
+        rec.Dx = Dx; rec.Dy = Dy; rec.elapsed_s = elapsed;
+        ctx->checks.push_back(rec);
+    }
+    if (o.verbose)
+        fprintf(stderr, "hpr k=%lld r=%lld t=%lld sigma=%.3e kkt=%.3e (p %.2e d %.2e g %.2e) R=%.3e cause=%d %.3fs\n",
+                (long long)(kk + 1), (long long)S.r, (long long)tl, S.sigma, kkt, errp, errd, gap, Rt,
+                cause, elapsed);
+
+    if (ctx->form == 1) S.iters_fp32 = kk + 1;
+    // the FP32 form hands over to FP64 iterates at the first check below switch_tol
+    const bool widen = ctx->form == 1 && !stop && kkt < o.switch_tol;
+    if (widen) ctx->form = 0;
+    if (restart && ctx->form == 1) {
+        k_restart32<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->xbar, ctx->ybar, ctx->x32,
+                                                    ctx->x0, ctx->y32, ctx->y0);
+        CKL();
+        ctx->launches += 1;
+    } else if (restart) {
+        k_restart<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->xbar, ctx->ybar, ctx->x,
+                                                  ctx->x0, ctx->y, ctx->y0);
+        CKL();
+        ctx->launches += 1;
+    } else if (widen) {
+        k_widen<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->x32, ctx->y32, ctx->x, ctx->y);
+        CKL();
+        ctx->launches += 1;
+    }
+    if (restart) {
+        S.sigma = sigma_next;
+        S.t = 0;
+        S.r++;
+    } else {
+        S.t = tl + 1;
+    }
+    if (S.tracing && kk < ctx->trace_n) {
+        st = trace_copy(ctx, kk);
+        if (st) return st;
+    }
+    S.k = kk + 1;
+    if (stop) {
+        S.done = true;
+    } else if (o.time_limit_s > 0.0 && elapsed >= o.time_limit_s && S.k < o.max_iter) {
+        S.status = HPR_TIME_LIMIT;
+        S.done = true;
+    } else if (S.k >= o.max_iter) {
+        S.done = true;
+    }
+    return HPR_OK;
+}
+
+// output: the last w_bar mapped back to the original LP, and the summary
+int solve_finish(hpr_ctx *ctx)
+{
+    SolveState &S = ctx->ss;
+    const int64_t n = ctx->n, m = ctx->m;
+    cudaStream_t s = ctx->stream;
     k_backmap<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->beta_b, ctx->beta_c, ctx->xbar,
                                               ctx->ybar, ctx->zbar, ctx->perm_c, ctx->perm_r, ctx->Dr,
                                               ctx->Dc, ctx->l_o, ctx->u_o, ctx->xo, ctx->yo, ctx->zo);
     CKL();
     ctx->launches += 1;
     CK(cudaStreamSynchronize(s));
-    const double total = now_s() - t0;
+    const double total = now_s() - S.t0;
 
     hpr_info &I = ctx->info;
     memset(&I, 0, sizeof I);
-    I.primal_obj = last_pobj; I.dual_obj = last_dobj; I.err_p = last_ep; I.err_d = last_ed;
-    I.err_gap = last_gap; I.kkt = last_kkt; I.sigma = sigma; I.lambda = lambda;
+    I.primal_obj = S.last_pobj; I.dual_obj = S.last_dobj; I.err_p = S.last_ep; I.err_d = S.last_ed;
+    I.err_gap = S.last_gap; I.kkt = S.last_kkt; I.sigma = S.sigma; I.lambda = S.lambda;
     I.solve_time_s = total; I.power_time_s = ctx->power_time;
-    I.time_to_1e4_s = time_1e4; I.iters_to_1e4 = iters_1e4;
-    I.iters = k; I.restarts = r; I.power_iters = ctx->power_iters;
-    I.n_checks = (int64_t)ctx->checks.size(); I.launches = ctx->launches; I.status = status;
-    I.iters_fp32 = iters_fp32;
+    I.time_to_1e4_s = S.time_1e4; I.iters_to_1e4 = S.iters_1e4;
+    I.iters = S.k; I.restarts = S.r; I.power_iters = ctx->power_iters;
+    I.n_checks = (int64_t)ctx->checks.size(); I.launches = ctx->launches; I.status = S.status;
+    I.iters_fp32 = S.iters_fp32;
     ctx->solved = true;
-    return status;
+    return S.status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hpr_solve(hpr_ctx *ctx, double tol)
+{
+    if (!ctx) return HPR_ERR_ARG;
+    if (!(tol > 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "tol must be > 0");
+    if (ctx->batched) return fail_arg(ctx, HPR_ERR_STATE, "the context belongs to a batch");
+    cudaSetDevice(ctx->device);
+    int st = solve_begin(ctx, tol);
+    if (st) return st;
+    SolveState &S = ctx->ss;
+    while (!S.done) {
+        if ((st = period_prepare(ctx))) return st;
+        if ((st = period_enqueue_own(ctx))) return st;
+        if ((st = period_readback(ctx))) return st;
+        CK(cudaStreamSynchronize(ctx->stream));
+        if ((st = period_after(ctx, now_s() - S.t0))) return st;
+    }
+    return solve_finish(ctx);
 }
 
 int hpr_get(const hpr_ctx *cctx, double *x, double *y, double *z, hpr_info *info)
@@ -1397,8 +1502,346 @@ void hpr_destroy(hpr_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    ctx->stream = ctx->home_stream;
     free_all(ctx);
     delete ctx;
+}
+
+}  // extern "C"
+
+// ====================================================================== batched solve
+// Many LPs, one context each, solved in lock step: every period, the normal iterations of
+// all contexts run as fused launches over one work list (k_sell_multi, captured as a CUDA
+// graph per period length and set of forms), while each context's check iterations,
+// residual passes and reductions, and its decisions, stay its own.  Contexts that have
+// converged drop out of the fused launches through their control blocks.
+
+struct hpr_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<hpr_ctx *> ctxs;
+    MultiUnit *unitsT = nullptr, *unitsA = nullptr;   // fused work lists (A^T and A phases)
+    int nunitsT = 0, nunitsA = 0;
+    SellArgs *sellT64 = nullptr, *sellA64 = nullptr, *sellT32 = nullptr, *sellA32 = nullptr;
+    EpiX<false> *ex = nullptr;
+    EpiY<false> *ey = nullptr;
+    EpiX32<false> *ex32 = nullptr;
+    EpiY32<false> *ey32 = nullptr;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (L, forms present)
+    int64_t power_threads = 8;
+    double solve_time = 0.0;
+    int64_t periods = 0, fused_launches = 0;
+};
+
+namespace {
+
+void batch_free(hpr_batch *b)
+{
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    void *dev[] = {b->unitsT, b->unitsA, b->sellT64, b->sellA64, b->sellT32, b->sellA32,
+                   b->ex, b->ey, b->ex32, b->ey32};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    for (hpr_ctx *c : b->ctxs) {
+        c->stream = c->home_stream;
+        c->batched = false;
+    }
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+template <class T>
+int upload_table(const std::vector<T> &h, T **d)
+{
+    if (cudaMalloc((void **)d, sizeof(T) * std::max<size_t>(1, h.size())) != cudaSuccess) return HPR_ERR_NOMEM;
+    if (!h.empty() && cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return HPR_ERR_CUDA;
+    return HPR_OK;
+}
+
+// fused work list of one phase: every context's units, costliest first (ties by context)
+std::vector<MultiUnit> fused_units(const std::vector<hpr_ctx *> &cs, bool transpose)
+{
+    struct U { float cost; int inst, run; };
+    std::vector<U> all;
+    for (size_t i = 0; i < cs.size(); ++i) {
+        const SellDev &M = transpose ? cs[i]->ST : cs[i]->SA;
+        if (M.rows == 0) continue;
+        for (int r = 0; r < M.nruns; ++r) all.push_back({M.ucost[(size_t)r], (int)i, r});
+    }
+    std::stable_sort(all.begin(), all.end(), [](const U &a, const U &b) { return a.cost > b.cost; });
+    std::vector<MultiUnit> out(all.size());
+    for (size_t i = 0; i < all.size(); ++i) out[i] = MultiUnit{all[i].inst, all[i].run};
+    return out;
+}
+
+// per-context layouts and epilogue operands of the fused launches (allocated once,
+// refreshed before every solve: a solve may reallocate a context's control block)
+int batch_tables(hpr_batch *b, bool alloc)
+{
+    std::vector<SellArgs> sT64, sA64, sT32, sA32;
+    std::vector<EpiX<false>> ex;
+    std::vector<EpiY<false>> ey;
+    std::vector<EpiX32<false>> ex32;
+    std::vector<EpiY32<false>> ey32;
+    for (hpr_ctx *c : b->ctxs) {
+        sT64.push_back(sell_of(c->ST, false));
+        sA64.push_back(sell_of(c->SA, false));
+        sT32.push_back(sell_of(c->ST, true));
+        sA32.push_back(sell_of(c->SA, true));
+        ex.push_back(epi_x<false>(c, 0));
+        ey.push_back(epi_y<false>(c, 0));
+        ex32.push_back(epi_x32<false>(c, 0));
+        ey32.push_back(epi_y32<false>(c, 0));
+    }
+    auto put = [&](auto &h, auto **d) -> int {
+        using T = typename std::remove_reference<decltype(h)>::type::value_type;
+        if (alloc && cudaMalloc((void **)d, sizeof(T) * h.size()) != cudaSuccess) return HPR_ERR_NOMEM;
+        if (cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) return HPR_ERR_CUDA;
+        return HPR_OK;
+    };
+    int st;
+    if ((st = put(sT64, &b->sellT64)) || (st = put(sA64, &b->sellA64)) || (st = put(sT32, &b->sellT32)) ||
+        (st = put(sA32, &b->sellA32)) || (st = put(ex, &b->ex)) || (st = put(ey, &b->ey)) ||
+        (st = put(ex32, &b->ex32)) || (st = put(ey32, &b->ey32)))
+        return st;
+    return HPR_OK;
+}
+
+template <class E>
+int launch_multi(hpr_batch *b, const MultiUnit *units, int nunits, const SellArgs *sells, const E *epis, int it)
+{
+    if (nunits == 0) return HPR_OK;
+    const int grid = (nunits + TB / 32 - 1) / (TB / 32);
+    k_sell_multi<E><<<grid, TB, 0, b->stream>>>(units, nunits, sells, epis, it);
+    if (cudaGetLastError() != cudaSuccess) return HPR_ERR_CUDA;
+    b->fused_launches += 1;
+    return HPR_OK;
+}
+
+// fused normal iterations 0 .. L-2 of a period (each context takes part in its own range)
+int enqueue_fused(hpr_batch *b, int L, int forms)
+{
+    int st;
+    for (int it = 0; it + 1 < L; ++it) {
+        if (forms & 1) {
+            if ((st = launch_multi(b, b->unitsT, b->nunitsT, b->sellT64, b->ex, it))) return st;
+        }
+        if (forms & 2) {
+            if ((st = launch_multi(b, b->unitsT, b->nunitsT, b->sellT32, b->ex32, it))) return st;
+        }
+        if (forms & 1) {
+            if ((st = launch_multi(b, b->unitsA, b->nunitsA, b->sellA64, b->ey, it))) return st;
+        }
+        if (forms & 2) {
+            if ((st = launch_multi(b, b->unitsA, b->nunitsA, b->sellA32, b->ey32, it))) return st;
+        }
+    }
+    return HPR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hpr_batch_create(hpr_batch **out, int64_t count, hpr_ctx *const *ctxs, void *cuda_stream)
+{
+    if (!out) return HPR_ERR_ARG;
+    *out = nullptr;
+    if (count < 1 || count > (1 << 20) || !ctxs) {
+        g_static_err = "hpr_batch_create: count outside [1, 2^20] or NULL context array";
+        return HPR_ERR_ARG;
+    }
+    std::vector<hpr_ctx *> cs(ctxs, ctxs + count);
+    for (size_t i = 0; i < cs.size(); ++i) {
+        if (!cs[i] || cs[i]->batched || cs[i]->device != cs[0]->device) {
+            g_static_err = "hpr_batch_create: NULL context, context already in a batch, or contexts on different devices";
+            return HPR_ERR_ARG;
+        }
+        for (size_t j = 0; j < i; ++j)
+            if (cs[j] == cs[i]) {
+                g_static_err = "hpr_batch_create: a context appears twice";
+                return HPR_ERR_ARG;
+            }
+    }
+    hpr_batch *b = new (std::nothrow) hpr_batch();
+    if (!b) return HPR_ERR_NOMEM;
+    b->device = cs[0]->device;
+    cudaSetDevice(b->device);
+    auto fail = [&](int code, const char *what) {
+        g_static_err = what;
+        batch_free(b);
+        delete b;
+        return code;
+    };
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(HPR_ERR_CUDA, "hpr_batch_create: cudaStreamCreate failed");
+        b->own_stream = true;
+    }
+    for (hpr_ctx *c : cs) cudaStreamSynchronize(c->stream);
+    b->ctxs = cs;
+    std::vector<MultiUnit> uT = fused_units(cs, true), uA = fused_units(cs, false);
+    int st = HPR_OK;
+    if ((st = upload_table(uT, &b->unitsT)) || (st = upload_table(uA, &b->unitsA)) ||
+        (st = batch_tables(b, true)))
+        return fail(st, "hpr_batch_create: device tables could not be allocated or copied");
+    b->nunitsT = (int)uT.size();
+    b->nunitsA = (int)uA.size();
+    for (hpr_ctx *c : cs) {
+        c->stream = b->stream;
+        c->batched = true;
+    }
+    *out = b;
+    return HPR_OK;
+}
+
+int hpr_batch_solve(hpr_batch *b, double tol)
+{
+    if (!b) return HPR_ERR_ARG;
+    if (!(tol > 0.0)) {
+        g_static_err = "hpr_batch_solve: tol must be > 0";
+        return HPR_ERR_ARG;
+    }
+    cudaSetDevice(b->device);
+    std::vector<hpr_ctx *> &cs = b->ctxs;
+    for (hpr_ctx *c : cs) {
+        if (c->opt.trace_iters > 0 || c->opt.check_every != cs[0]->opt.check_every) {
+            g_static_err = "hpr_batch_solve: tracing is not available in a batch, and all contexts need the same check_every";
+            return HPR_ERR_ARG;
+        }
+    }
+    const double t0 = now_s();
+    b->periods = 0;
+    b->fused_launches = 0;
+    // power methods: each context on a stream of its worker thread, workers in parallel
+    {
+        const int W = (int)std::max<int64_t>(1, std::min<int64_t>(b->power_threads, (int64_t)cs.size()));
+        std::vector<int> rc((size_t)W, HPR_OK);
+        std::vector<std::thread> pool;
+        for (int w = 0; w < W; ++w) {
+            pool.emplace_back([&, w]() {
+                cudaSetDevice(b->device);
+                cudaStream_t ws = nullptr;
+                if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+                    rc[(size_t)w] = HPR_ERR_CUDA;
+                    return;
+                }
+                for (size_t i = (size_t)w; i < cs.size() && rc[(size_t)w] == HPR_OK; i += (size_t)W) {
+                    hpr_ctx *c = cs[i];
+                    c->stream = ws;
+                    rc[(size_t)w] = solve_begin(c, tol);
+                    cudaStreamSynchronize(ws);
+                    c->stream = b->stream;
+                }
+                cudaStreamDestroy(ws);
+            });
+        }
+        for (auto &th : pool) th.join();
+        for (int v : rc)
+            if (v != HPR_OK) return v;
+    }
+    int st = batch_tables(b, false);
+    if (st) {
+        g_static_err = "hpr_batch_solve: device tables could not be refreshed";
+        return st;
+    }
+    for (hpr_ctx *c : cs) c->ss.ctl_off = false;
+    for (;;) {
+        std::vector<hpr_ctx *> act;
+        for (hpr_ctx *c : cs)
+            if (!c->ss.done) act.push_back(c);
+        if (act.empty()) break;
+        int forms = 0;
+        for (hpr_ctx *c : cs) {
+            if (c->ss.done) {                // once: its control block takes it out of fused launches
+                if (!c->ss.ctl_off && (st = period_prepare(c))) return st;
+                c->ss.ctl_off = true;
+                continue;
+            }
+            if ((st = period_prepare(c))) return st;
+            forms |= c->form == 1 ? 2 : 1;
+        }
+        const int L = act[0]->ss.L;
+        for (hpr_ctx *c : act)
+            if (c->ss.L != L) {
+                g_static_err = "hpr_batch_solve: contexts out of step";
+                return HPR_ERR_STATE;
+            }
+        // iteration 0 in check mode for contexts that start an inner loop
+        if (L > 1)
+            for (hpr_ctx *c : act)
+                if (c->ss.first_r0 && (st = enqueue_iteration(c, 0, true, true, 0))) return st;
+        // fused normal iterations 0 .. L-2
+        if (L > 1) {
+            const auto key = std::make_pair(L, forms);
+            auto itg = b->graphs.find(key);
+            if (itg == b->graphs.end()) {
+                if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HPR_ERR_CUDA;
+                const int64_t before = b->fused_launches;
+                int rr = enqueue_fused(b, L, forms);
+                b->fused_launches = before;
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+                if (rr || e != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    g_static_err = "hpr_batch_solve: graph capture failed";
+                    return rr ? rr : HPR_ERR_CUDA;
+                }
+                cudaGraphExec_t ex = nullptr;
+                e = cudaGraphInstantiate(&ex, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    g_static_err = "hpr_batch_solve: graph instantiation failed";
+                    return HPR_ERR_CUDA;
+                }
+                itg = b->graphs.emplace(key, ex).first;
+            }
+            if (cudaGraphLaunch(itg->second, b->stream) != cudaSuccess) return HPR_ERR_CUDA;
+            b->fused_launches += (int64_t)(L - 1) * (((forms & 1) ? 2 : 0) + ((forms & 2) ? 2 : 0));
+        }
+        // the check iteration, per context
+        for (hpr_ctx *c : act) {
+            if ((st = enqueue_iteration(c, L - 1, true, true, 1))) return st;
+            if ((st = period_readback(c))) return st;
+        }
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+            g_static_err = "hpr_batch_solve: CUDA error during a period";
+            return HPR_ERR_CUDA;
+        }
+        for (hpr_ctx *c : act)
+            if ((st = period_after(c, now_s() - c->ss.t0))) return st;
+        b->periods++;
+    }
+    int worst = HPR_OK;
+    for (hpr_ctx *c : cs) {
+        st = solve_finish(c);
+        if (st < 0) return st;
+        if (st != HPR_OK) worst = st;
+    }
+    b->solve_time = now_s() - t0;
+    return worst;
+}
+
+int hpr_batch_stats(const hpr_batch *b, double *solve_time_s, int64_t *periods, int64_t *fused_launches)
+{
+    if (!b) return HPR_ERR_ARG;
+    if (solve_time_s) *solve_time_s = b->solve_time;
+    if (periods) *periods = b->periods;
+    if (fused_launches) *fused_launches = b->fused_launches;
+    return HPR_OK;
+}
+
+void hpr_batch_destroy(hpr_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
 }
 
 }  // extern "C"

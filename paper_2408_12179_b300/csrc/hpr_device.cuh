@@ -52,7 +52,11 @@ enum {
 struct DevCtl {
     double sigma;     // sigma_r
     double inv_ls;    // 1 / (lambda sigma_r)
-    double pad[6];
+    int fused_lo, fused_hi;   // iterations [fused_lo, fused_hi) of the period that fused
+                              // (batched) launches run for this context
+    int form;         // 0: FP64 iterates, 1: FP32 form
+    int active;       // 0: the context's solve has ended (fused launches skip it)
+    double pad[4];
     double h[2];      // h[2i] = 1/(t+2), h[2i+1] = (t+1)/(t+2) for iteration i of the period
 };
 
@@ -189,20 +193,11 @@ struct SellArgs {
 // vectors, NV gathered vectors xa (, xb), NP partial sums (ids q[]), a Pre record of
 // epilogue operands (prefetch(j)) and row(j, act, s, pre, part) with FP64 row sums s.
 template <class E>
-__global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
+__device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int run, double *part)
 {
-    constexpr int NV = E::NV, NP = E::NP;
+    constexpr int NV = E::NV;
     using V = typename E::Val;
-    __shared__ double red[TB / 32];
-    if (S.skip && *S.skip) return;
-    E ee = e;
-    ee.load();
     const int lane = threadIdx.x & 31;
-    const int run = blockIdx.x * (TB / 32) + (threadIdx.x >> 5);   // one unit per warp
-    double part[NP > 0 ? NP : 1];
-#pragma unroll
-    for (int i = 0; i < (NP > 0 ? NP : 1); ++i) part[i] = 0.0;
-
     int buf_r0 = 0, buf_n = 0;                   // rows [buf_r0, buf_r0 + buf_n) hold sums
     double buf0 = 0.0, buf1 = 0.0;               // lane t: sum of row buf_r0 + t
     typename E::Pre pre{};
@@ -305,7 +300,21 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
             buf_n = 0;
         }
     }
+}
 
+template <class E>
+__global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
+{
+    constexpr int NP = E::NP;
+    __shared__ double red[TB / 32];
+    if (S.skip && *S.skip) return;
+    E ee = e;
+    ee.load();
+    const int run = blockIdx.x * (TB / 32) + (threadIdx.x >> 5);   // one unit per warp
+    double part[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int i = 0; i < (NP > 0 ? NP : 1); ++i) part[i] = 0.0;
+    sell_unit(S, ee, run, part);
     if (NP > 0) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
@@ -313,6 +322,35 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
             if (threadIdx.x == 0) ee.partials[ee.q[i] * ee.pstride + blockIdx.x] = t;
         }
     }
+}
+
+// Many LPs in one launch (the batched solve): unit u of the fused work list is work unit
+// units[u].run of context units[u].inst, whose layout and epilogue operands come from
+// the per-context tables.  A warp skips its unit unless that context is active, in the
+// form this kernel computes, and iteration `it` of the period is one of its fused ones
+// (its control block says which).  Normal iterations only (no partial sums).
+struct MultiUnit {
+    int inst, run;
+};
+
+template <class E>
+__global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell_multi(const MultiUnit *__restrict__ units,
+                                                                  int nunits, const SellArgs *__restrict__ sells,
+                                                                  const E *__restrict__ epis, int it)
+{
+    static_assert(E::NP == 0, "fused launches run normal iterations only");
+    constexpr int FORM = sizeof(typename E::Val) == 4 ? 1 : 0;
+    const int u = blockIdx.x * (TB / 32) + (threadIdx.x >> 5);
+    if (u >= nunits) return;                      // whole warps: no block-wide step follows
+    const MultiUnit mu = units[u];
+    E ee = epis[mu.inst];
+    const DevCtl *c = ee.ctl;
+    if (!c->active || c->form != FORM || it < c->fused_lo || it >= c->fused_hi) return;
+    ee.it = it;
+    ee.load();
+    const SellArgs S = sells[mu.inst];
+    double part[1] = {0.0};
+    sell_unit(S, ee, mu.run, part);
 }
 
 // ------------------------------------------------------------------ epilogues

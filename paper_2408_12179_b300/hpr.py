@@ -90,6 +90,11 @@ SIGNATURES = {
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                          ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, _D, _I64]),
+    "hpr_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    "hpr_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "hpr_batch_stats": (ctypes.c_int, [ctypes.c_void_p, _D, _I64, _I64]),
+    "hpr_batch_destroy": (None, [ctypes.c_void_p]),
     "hpr_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hpr_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "hpr_destroy": (None, [ctypes.c_void_p]),
@@ -283,12 +288,55 @@ class Solver:
     def trace(self, k):
         return hpr_get_trace(self.ctx, k, self.n, self.m)
 
+    def result(self):
+        """(x, y, z, info) of the last solve (e.g. one run through a Batch)."""
+        x, y, z, info = hpr_get(self.ctx, self.n, self.m)
+        return dict(x=x, y=y, z=z, info=info, status=int(info["status"]))
+
     def time_iteration(self, reps=50):
         return hpr_time_iteration(self.ctx, reps)
 
     def close(self):
         hpr_destroy(self.ctx)
         self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Context manager solving several Solver contexts in lock step with fused launches
+    (hpr_batch_*).  The solvers stay owned by the caller and must outlive the batch."""
+
+    def __init__(self, solvers, stream=None):
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
+        out = ctypes.c_void_p()
+        code = load().hpr_batch_create(ctypes.byref(out), len(self.solvers), arr, stream)
+        _check(code, None)
+        self.b = out
+
+    def solve(self, tol=1e-8):
+        """Returns the batch status and the per-LP results."""
+        status = load().hpr_batch_solve(self.b, float(tol))
+        if status < 0:
+            _check(status, None)
+        return status, [s.result() for s in self.solvers]
+
+    def stats(self):
+        t = ctypes.c_double()
+        p = ctypes.c_int64()
+        f = ctypes.c_int64()
+        _check(load().hpr_batch_stats(self.b, ctypes.byref(t), ctypes.byref(p), ctypes.byref(f)), None)
+        return dict(solve_time_s=t.value, periods=p.value, fused_launches=f.value)
+
+    def close(self):
+        if self.b is not None and self.b.value:
+            load().hpr_batch_destroy(self.b)
+        self.b = None
 
     def __enter__(self):
         return self

@@ -197,6 +197,24 @@ def planted_medium(seed: int, scale: float = 1.0) -> LP:
     return planted_sparse(seed, m=m + (m % 2), n=n, nnz=nnz, cap=cap)
 
 
+def batch_family(seed: int, count: int, m_lo: int = 500, m_hi: int = 50_000) -> list[LP]:
+    """Uneven LPs for a batched solve: m log-uniform in [m_lo, m_hi] (rounded to even),
+    n = 2.5 m, density log-uniform in [0.1%, 1%], each built like the medium planted LP
+    (Zipf(1.5) column counts capped at min(2000, m), values +-10^U(-3,3), 20% free
+    columns, planted optimum) with nnz = density * m * n."""
+    rng = np.random.default_rng([0xBA7C, seed])
+    out = []
+    for i in range(count):
+        m = int(round(math.exp(rng.uniform(math.log(m_lo), math.log(m_hi)))))
+        m += m % 2
+        n = int(round(2.5 * m))
+        density = math.exp(rng.uniform(math.log(1e-3), math.log(1e-2)))
+        lp = planted_sparse(seed * 1_000_003 + i, m=m, n=n, nnz=density * m * n, cap=max(2, min(2000, m)))
+        lp.name = f"batch-{seed}-{i}-m{m}"
+        out.append(lp)
+    return out
+
+
 def micro_lp(seed: int, n: int = 5, m1: int = 1, m2: int = 3) -> LP:
     """Micro LP with finite bounds and a dense A, feasible by construction (the
     right-hand sides are taken at a random point of the box).  No optimum is planted:

@@ -1,0 +1,100 @@
+"""The batched solve (many LPs in lock step, normal iterations fused into shared launches)
+through the C ABI.  Each LP's arithmetic is the same as in its own solve -- the same
+layout, the same per-row operation order, the same per-context checks and reductions --
+so every batched result must equal the context's solo result bit for bit, and (through
+the solo path's parity) the oracle's to the usual tolerances, which is also checked."""
+import numpy as np
+import pytest
+
+from paper_2408_12179_b300 import hpr, lpgen
+
+pytestmark = pytest.mark.gpu
+
+import oracle
+from oracle import kkt as K
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    hpr.load()
+
+
+def _family(with_slow=True):
+    """Uneven LPs: tiny, medium at 1/100, a 300-node multicommodity flow, an
+    inequality-only LP, and (with_slow) four of the batched family, which need several
+    hundred thousand iterations to 1e-8 and stop at the iteration cap here."""
+    lps = [lpgen.planted_tiny(0), lpgen.planted_tiny(1, m1=10, m2=200, n=300, density=0.03),
+           lpgen.planted_medium(2, 0.01), lpgen.mcf_lp(0, nodes=300),
+           lpgen.planted_tiny(3, m1=0, m2=90, n=170)]
+    if with_slow:
+        lps += lpgen.batch_family(7, 4, 500, 2000)
+    return lps
+
+
+CAP = 20_000
+
+
+def _solo(lp, **opts):
+    with hpr.Solver(lp, **opts) as s:
+        return s.solve(1e-8)
+
+
+@pytest.mark.parametrize("precisions", ["fp64", "mixed"])
+def test_batch_equals_solo_solves(precisions):
+    lps = _family()
+    prec = [0] * len(lps) if precisions == "fp64" else [i % 2 for i in range(len(lps))]
+    solvers = [hpr.Solver(lp, precision=p, max_iter=CAP) for lp, p in zip(lps, prec)]
+    try:
+        with hpr.Batch(solvers) as b:
+            status, res = b.solve(1e-8)
+            st = b.stats()
+        assert status == hpr.HPR_MAX_ITER            # the slow ones stop at the cap
+        assert st["periods"] > 0 and st["fused_launches"] > 0
+        assert sum(r["status"] == hpr.HPR_OK for r in res) >= 4
+        for lp, p, r in zip(lps, prec, res):
+            solo = _solo(lp, precision=p, max_iter=CAP)
+            assert r["status"] == solo["status"], lp.name
+            assert r["info"]["iters"] == solo["info"]["iters"], lp.name
+            assert r["info"]["restarts"] == solo["info"]["restarts"], lp.name
+            for key in ("x", "y", "z"):
+                assert np.array_equal(r[key], solo[key]), (lp.name, key)
+    finally:
+        for s in solvers:
+            s.close()
+
+
+def test_batch_results_match_oracle():
+    lps = _family(with_slow=False)
+    solvers = [hpr.Solver(lp) for lp in lps]
+    try:
+        with hpr.Batch(solvers) as b:
+            status, res = b.solve(1e-8)
+        assert status == hpr.HPR_OK
+        for lp, r in zip(lps, res):
+            ref = oracle.solve(lp, tol=1e-8, max_iter=400_000)
+            ind = K.kkt(lp, r["x"], r["y"], r["z"])
+            assert ind["kkt"] <= 1e-8 * (1 + 1e-6), lp.name
+            assert abs(r["info"]["primal_obj"] - ref["info"]["pobj"]) <= 1e-7 * abs(ref["info"]["pobj"]), lp.name
+            assert K.in_C(r["x"], lp.l, lp.u) and K.in_D(r["y"], lp.m1)
+    finally:
+        for s in solvers:
+            s.close()
+
+
+def test_batch_misuse_is_rejected():
+    a = hpr.Solver(lpgen.planted_tiny(0))
+    c = hpr.Solver(lpgen.planted_tiny(1), check_every=100)
+    try:
+        with pytest.raises(hpr.HprError):
+            hpr.Batch([a, a])
+        with hpr.Batch([a, c]) as b:
+            with pytest.raises(hpr.HprError) as e:
+                a.solve(1e-8)                         # a context in a batch is not solved alone
+            assert e.value.code == hpr.HPR_ERR_STATE
+            with pytest.raises(hpr.HprError):
+                b.solve(1e-8)                         # different check periods
+        # after the batch is gone the contexts work on their own again
+        assert a.solve(1e-8)["status"] == hpr.HPR_OK
+    finally:
+        a.close()
+        c.close()
