@@ -17,6 +17,7 @@ on a bounded sample of the same workload.
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -232,7 +233,25 @@ def run_batch(args):
     lps = lpgen.batch_family(args.seed + rank, args.count, 500, m_hi)
     stream = torch.cuda.Stream()
     opts = dict(tol=args.tol, precision=args.precision, **VARIANTS[args.variant])
-    solvers = [hpr.Solver(lp, max_iter=args.max_iter, **opts) for lp in lps]
+    t_create = time.perf_counter()
+    if args.autotune:
+        # one autotuned context per size bucket (floor(log2 nnz)); its layout is reused
+        tuned = {}
+        solvers = []
+        for lp in lps:
+            bucket = int(math.floor(math.log2(max(lp.nnz, 1))))
+            if bucket not in tuned:
+                s_ = hpr.Solver(lp, max_iter=args.max_iter, autotune=1, **opts)
+                lay = s_.layout()
+                tuned[bucket] = dict(sell_steps_a=lay["sell_steps"][0], sell_steps_t=lay["sell_steps"][1],
+                                     unit_cost_a=lay["unit_cost"][0], unit_cost_t=lay["unit_cost"][1])
+            else:
+                s_ = hpr.Solver(lp, max_iter=args.max_iter, **tuned[bucket], **opts)
+            solvers.append(s_)
+    else:
+        tuned = None
+        solvers = [hpr.Solver(lp, max_iter=args.max_iter, **opts) for lp in lps]
+    create_secs = time.perf_counter() - t_create
     batch = hpr.Batch(solvers, stream.cuda_stream)
     for s_ in solvers:
         s_.set_options(max_iter=300)
@@ -279,7 +298,9 @@ def run_batch(args):
         "config": {"workload": f"batch of {len(lps)} uneven planted LPs (m log-uniform in [500, {m_hi}], "
                                f"n = 2.5 m, density log-uniform in [0.1%, 1%], medium-LP value rules; "
                                f"total nnz {nnz}, seed {args.seed})",
-                   "tol": args.tol, "max_iter": args.max_iter, "variant": args.variant},
+                   "tol": args.tol, "max_iter": args.max_iter, "variant": args.variant,
+                   "autotune": ({str(k): v for k, v in sorted(tuned.items())} if tuned else None),
+                   "create_s": create_secs},
         "batch_status": hpr.hpr_status_str(int(status)), "converged": len(conv), "count": len(lps),
         "time_to_all_s": secs, "iters_summed": iters, "iters_per_s_summed": iters / secs,
         "periods": st["periods"], "gpu_launches": int(st["fused_launches"] + sum(int(r["info"]["launches"]) for r in res)),
@@ -341,7 +362,10 @@ def run_ours(args):
     if args.lambda_fixed > 0:
         opts["lambda_fixed"] = args.lambda_fixed   # profiling aid: skips the power method
     opts.update(VARIANTS[args.variant])
+    if args.autotune:
+        opts["autotune"] = 1
     solver = hpr.Solver(lp, **opts)
+    layout = solver.layout()
 
     def barrier():
         torch.cuda.synchronize()
@@ -426,11 +450,14 @@ def run_ours(args):
 
     t8 = [i["solve_time_s"] for i in infos]
     t4 = [i["time_to_1e4_s"] for i in infos]
+    cfg = config_dict(args, lp)
+    if args.autotune:
+        cfg["layout"] = layout
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
-        "data": "synthetic", "config": config_dict(args, lp),
+        "data": "synthetic", "config": cfg,
         "time_to_kkt_1e-8_s": statistics.mean(t8), "time_to_kkt_1e-4_s": statistics.mean(t4),
         "iters_to_kkt_1e-8": infos[-1]["iters"], "iters_to_kkt_1e-4": infos[-1]["iters_to_1e4"],
         "status": hpr.hpr_status_str(int(infos[-1]["status"])), "final_kkt": infos[-1]["kkt"],
@@ -480,6 +507,9 @@ def main():
                          "(1M nodes at scale 1), or a batch of uneven planted LPs solved in one "
                          "batched run (m log-uniform in [500, 50000 * scale])")
     ap.add_argument("--count", type=int, default=512, help="LPs in the batch workload")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the sliced-ELL layouts by timing candidates at creation (batch workload: "
+                         "once per size bucket of nnz, reused for the bucket's other LPs)")
     ap.add_argument("--solo-sample", dest="solo_sample", type=int, default=16,
                     help="batch workload: LPs also solved one by one, and as a batch of their own")
     ap.add_argument("--variant", choices=list(VARIANTS), default="hpr",

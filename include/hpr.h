@@ -96,6 +96,15 @@ typedef struct {
                                  Algorithm 2 (default); 0: w_target = w_bar (the DR and
                                  HDR variants of the Section 4.2 ablation).  The y step
                                  uses A(2 x_bar - x) either way (eq. update-y-2) */
+    int64_t autotune;         /* 1: at hpr_create, time the phase kernels with candidate
+                                 sliced-ELL layouts (lanes-per-row bound 16..128, work-unit
+                                 size 32..256) for A and A^T and keep the fastest; 0 (default):
+                                 the layouts given below */
+    int64_t sell_steps_a, sell_steps_t;  /* lanes-per-row bound of A's / A^T's layout: a group
+                                 of 32 rows uses the fewest lanes per row (1..32) that keep
+                                 its longest row within this many steps; 0: 40 */
+    double unit_cost_a, unit_cost_t;     /* work-unit size of A's / A^T's layout (a group
+                                 costlier than this is split into one unit per slice); 0: 64 */
 } hpr_options;
 
 /* Result summary (original, unscaled problem). */
@@ -206,6 +215,11 @@ int hpr_power_noalloc(int64_t m, int64_t n, const int32_t *A_row_ptr, const int3
                       const double *A_val, const int32_t *At_row_ptr, const int32_t *At_col_idx,
                       const double *At_val, uint64_t seed, int64_t max_iter, double tol,
                       double *u, double *s, void *cuda_stream, double *lambda, int64_t *iters);
+
+/* Layout of the context's sliced-ELL copies (after autotuning, if asked): for A (index 0)
+ * and A^T (index 1) the lanes-per-row bound, the work-unit size and the number of work
+ * units; any pointer may be NULL. */
+int hpr_get_layout(const hpr_ctx *ctx, int64_t *sell_steps, double *unit_cost, int64_t *units);
 
 /* ---- Batched solve (no counterpart in the paper: many independent LPs in lock step).
  * A batch takes `count` contexts made by hpr_create (their LPs may differ in size and

@@ -55,6 +55,8 @@ struct GraphKey {
 struct SellDev {
     int rows = 0, nslices = 0;
     int64_t entries = 0;          // stored entries (nonzeros + padding)
+    int steps_max = 0;            // layout parameters (build_sell)
+    double unit_cost = 0.0;
     int nruns = 0;                // work units (one per warp)
     int grid = 0;                 // CTAs of a sliced-ELL launch: ceil(nruns / warps per CTA)
     int *srow = nullptr, *sptr = nullptr, *wstart = nullptr, *col = nullptr;
@@ -223,9 +225,9 @@ std::vector<int> order_by_length(const std::vector<int> &rp, int rows)
 // Sliced-ELL layout of a CSR matrix (rows in the order perm, longest first; columns
 // renamed by icol): host index arrays; the values are gathered on the GPU through `src`.
 // Rows are taken in groups of 32; a group uses L lanes per row, L the smallest power of
-// two that keeps its widest slice within SELL_STEPS steps (L <= 32), and is stored as L
+// two that keeps its widest slice within `steps_max` steps (L <= 32), and is stored as L
 // slices of 32 / L rows.  Work units (one per warp): a group whole, or each slice of a
-// group whose cost exceeds UNIT_COST.
+// group whose cost exceeds `unit_cost`.  Defaults 40 and 64; the autotuner may pick others.
 constexpr int SELL_STEPS = 40;
 constexpr double UNIT_COST = 64.0;
 
@@ -234,12 +236,17 @@ struct SellHost {
     std::vector<int> srow, sptr, col, src, wstart;
     std::vector<unsigned char> slg;
     std::vector<float> ucost;        // cost of each work unit (steps + epilogue share)
+    int steps_max = SELL_STEPS;
+    double unit_cost = UNIT_COST;
 };
 
 SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int rows,
-                    const std::vector<int> &perm, const std::vector<int> &icol)
+                    const std::vector<int> &perm, const std::vector<int> &icol,
+                    int steps_max = SELL_STEPS, double unit_cost = UNIT_COST)
 {
     SellHost h;
+    h.steps_max = steps_max;
+    h.unit_cost = unit_cost;
     auto len = [&](int i) { return rp[(size_t)perm[(size_t)i] + 1] - rp[(size_t)perm[(size_t)i]]; };
     std::vector<double> scost;       // cost of each slice (epilogue share included)
     std::vector<int> gfirst;         // first slice of each group
@@ -249,7 +256,7 @@ SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int 
         const int g1 = std::min(rows, g0 + 32);
         const int lmax = len(g0);
         int lg = 0;
-        while (lg < 5 && (lmax + (1 << lg) - 1) / (1 << lg) > SELL_STEPS) ++lg;
+        while (lg < 5 && (lmax + (1 << lg) - 1) / (1 << lg) > steps_max) ++lg;
         const int L = 1 << lg, per = 32 / L;
         gfirst.push_back(h.nslices);
         for (int r = g0; r < g1; r += per) {
@@ -279,7 +286,7 @@ SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int 
     for (size_t g = 0; g + 1 < gfirst.size(); ++g) {
         double gc = 0.0;
         for (int sl = gfirst[g]; sl < gfirst[g + 1]; ++sl) gc += scost[(size_t)sl];
-        if (gc <= UNIT_COST) {
+        if (gc <= unit_cost) {
             h.wstart.push_back(gfirst[g]);
             h.ucost.push_back((float)gc);
         } else {
@@ -639,6 +646,126 @@ int run_power(hpr_ctx *ctx)
 
 // ---------------------------------------------------------------- create helpers
 
+void free_layout(SellDev &D)
+{
+    void *p[] = {D.srow, D.sptr, D.wstart, D.slg, D.col, D.val, D.val32, D.src};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    D.srow = D.sptr = D.wstart = D.col = D.src = nullptr;
+    D.slg = nullptr;
+    D.val = nullptr;
+    D.val32 = nullptr;
+}
+
+// device copy of a host layout, with values gathered from the scaled CSR values
+int install_layout(hpr_ctx *ctx, SellDev &D, const SellHost &H, int rows, const double *csr_val)
+{
+    cudaStream_t s = ctx->stream;
+    free_layout(D);
+    D.rows = rows; D.nslices = H.nslices;
+    D.steps_max = H.steps_max; D.unit_cost = H.unit_cost;
+    D.nruns = (int)H.wstart.size() - 1;
+    D.ucost = H.ucost;
+    D.grid = std::max(1, (D.nruns + TB / 32 - 1) / (TB / 32));
+    D.entries = (int64_t)H.col.size();
+    DALLOC(D.val32, D.entries);
+    DALLOC(D.srow, (int64_t)H.srow.size()); DALLOC(D.sptr, (int64_t)H.sptr.size());
+    DALLOC(D.wstart, (int64_t)H.wstart.size()); DALLOC(D.slg, (int64_t)H.slg.size());
+    DALLOC(D.col, D.entries); DALLOC(D.val, D.entries); DALLOC(D.src, D.entries);
+    CK(cudaMemcpyAsync(D.srow, H.srow.data(), sizeof(int) * H.srow.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.sptr, H.sptr.data(), sizeof(int) * H.sptr.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.wstart, H.wstart.data(), sizeof(int) * H.wstart.size(), cudaMemcpyHostToDevice, s));
+    if (!H.slg.empty()) CK(cudaMemcpyAsync(D.slg, H.slg.data(), H.slg.size(), cudaMemcpyHostToDevice, s));
+    if (D.entries) {
+        CK(cudaMemcpyAsync(D.col, H.col.data(), sizeof(int) * H.col.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(D.src, H.src.data(), sizeof(int) * H.src.size(), cudaMemcpyHostToDevice, s));
+        k_gather_src<<<grid_for(D.entries), 256, 0, s>>>(D.entries, csr_val, D.src, D.val); CKL();
+        k_narrow<<<grid_for(D.entries), 256, 0, s>>>(D.entries, D.val, D.val32); CKL();
+    }
+    CK(cudaStreamSynchronize(s));
+    return HPR_OK;
+}
+
+// average duration (ms) of a plain phase launch with the current layout: 2 launches to
+// warm up, then 5 back to back between CUDA events (the values do not change the timing)
+int time_phase(hpr_ctx *ctx, bool transpose, double *ms)
+{
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int st = HPR_OK;
+    for (int r = 0; r < 7 && st == HPR_OK; ++r) {
+        if (r == 2) cudaEventRecord(e0, ctx->stream);
+        st = transpose ? launch_sell(ctx, ctx->ST, epi_x<false>(ctx, 0)) : launch_sell(ctx, ctx->SA, epi_y<false>(ctx, 0));
+    }
+    cudaEventRecord(e1, ctx->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (st == HPR_OK && e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "time_phase", __LINE__);
+    *ms = t / 5.0;
+    return HPR_OK;
+}
+
+// The autotuner: for one matrix (A: the y phase, A^T: the x phase) time the phase kernel
+// with the layout built for each lanes-per-row bound (steps_max 16 ... 128), then each unit
+// size (unit_cost 32 ... 256) at the best bound, and keep the fastest layout (a candidate
+// replaces the incumbent only when at least 2% faster).  Runs at creation, before any
+// solve; the iterate vectors are zeroed first.
+int autotune_layout(hpr_ctx *ctx, bool transpose, const std::vector<int> &rp, const std::vector<int> &ci,
+                    const std::vector<int> &perm, const std::vector<int> &icol)
+{
+    SellDev &D = transpose ? ctx->ST : ctx->SA;
+    if (D.rows == 0) return HPR_OK;
+    const int rows = D.rows;
+    const double *csr_val = transpose ? ctx->T_val : ctx->A_val;
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemsetAsync(ctx->x, 0, sizeof(double) * ctx->n, s));
+    CK(cudaMemsetAsync(ctx->x0, 0, sizeof(double) * ctx->n, s));
+    CK(cudaMemsetAsync(ctx->xhat, 0, sizeof(double) * ctx->n, s));
+    CK(cudaMemsetAsync(ctx->y, 0, sizeof(double) * ctx->m, s));
+    CK(cudaMemsetAsync(ctx->y0, 0, sizeof(double) * ctx->m, s));
+    CK(cudaMemcpyAsync(ctx->ctl, ctx->ctl_h, ctx->ctl_bytes, cudaMemcpyHostToDevice, s));
+    int best_steps = D.steps_max;
+    double best_cost = D.unit_cost, best_ms = 0.0;
+    int st = time_phase(ctx, transpose, &best_ms);
+    if (st) return st;
+    auto trial = [&](int steps, double cost) -> int {
+        if (steps == best_steps && cost == best_cost) return HPR_OK;
+        SellHost H = build_sell(rp, ci, rows, perm, icol, steps, cost);
+        int r = install_layout(ctx, D, H, rows, csr_val);
+        if (r) return r;
+        double ms = 0.0;
+        if ((r = time_phase(ctx, transpose, &ms))) return r;
+        if (ms < 0.98 * best_ms) {
+            best_ms = ms;
+            best_steps = steps;
+            best_cost = cost;
+        }
+        return HPR_OK;
+    };
+    for (int steps : {16, 24, 40, 64, 128})
+        if ((st = trial(steps, best_cost))) return st;
+    for (double cost : {32.0, 64.0, 128.0, 256.0})
+        if ((st = trial(best_steps, cost))) return st;
+    if (D.steps_max != best_steps || D.unit_cost != best_cost) {
+        SellHost H = build_sell(rp, ci, rows, perm, icol, best_steps, best_cost);
+        if ((st = install_layout(ctx, D, H, rows, csr_val))) return st;
+    }
+    // the partial sums of the check kernels need one slot per CTA of the larger grid
+    const int need = std::max(ctx->SA.grid, ctx->ST.grid);
+    if (need > ctx->pstride) {
+        cudaFree(ctx->partials);
+        ctx->partials = nullptr;
+        ctx->pstride = need;
+        DALLOC(ctx->partials, (int64_t)NQ * ctx->pstride);
+    }
+    return HPR_OK;
+}
+
 int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const double *b1,
                        const double *b2, const double *c, const double *l, const double *u)
 {
@@ -683,8 +810,13 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     std::vector<int> ipr((size_t)m), ipc((size_t)n);
     for (int64_t i = 0; i < m; ++i) ipr[(size_t)pr[(size_t)i]] = (int)i;
     for (int64_t j = 0; j < n; ++j) ipc[(size_t)pc[(size_t)j]] = (int)j;
-    SellHost hA = build_sell(rp, ci, (int)m, pr, ipc);
-    SellHost hT = build_sell(trp, tci, (int)n, pc, ipr);
+    const hpr_options &op = ctx->opt;
+    const int stepsA = op.sell_steps_a > 0 ? (int)op.sell_steps_a : SELL_STEPS;
+    const int stepsT = op.sell_steps_t > 0 ? (int)op.sell_steps_t : SELL_STEPS;
+    const double costA = op.unit_cost_a > 0.0 ? op.unit_cost_a : UNIT_COST;
+    const double costT = op.unit_cost_t > 0.0 ? op.unit_cost_t : UNIT_COST;
+    SellHost hA = build_sell(rp, ci, (int)m, pr, ipc, stepsA, costA);
+    SellHost hT = build_sell(trp, tci, (int)n, pc, ipr, stepsT, costT);
     std::vector<unsigned char> ineq((size_t)m);
     for (int64_t i = 0; i < m; ++i) ineq[(size_t)i] = pr[(size_t)i] >= m1 ? 1 : 0;
     {
@@ -707,6 +839,7 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     ctx->pstride = std::max({gA, gT, (int)((std::max(m, n) + TB - 1) / TB), 1});
     auto upload_sell = [&](SellDev &D, const SellHost &H, int rows) -> int {
         D.rows = rows; D.nslices = H.nslices;
+        D.steps_max = H.steps_max; D.unit_cost = H.unit_cost;
         D.nruns = (int)H.wstart.size() - 1;
         D.ucost = H.ucost;
         D.grid = std::max(1, (D.nruns + TB / 32 - 1) / (TB / 32));
@@ -821,6 +954,12 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     k_permute<<<gn, 256, 0, s>>>(n, ctx->u_s, ctx->perm_c, ctx->up); CKL();
     k_permute<<<gn, 256, 0, s>>>(n, ctx->wc, ctx->perm_c, ctx->wcp); CKL();
     CK(cudaStreamSynchronize(s));
+    if (ctx->opt.autotune) {
+        int r1 = autotune_layout(ctx, false, rp, ci, pr, ipc);
+        if (r1) return r1;
+        r1 = autotune_layout(ctx, true, trp, tci, pc, ipr);
+        if (r1) return r1;
+    }
     return HPR_OK;
 }
 
@@ -865,6 +1004,9 @@ int hpr_default_options(hpr_options *o)
     o->switch_tol = 1e-5;
     o->halpern = 1;
     o->reflect = 1;
+    o->autotune = 0;
+    o->sell_steps_a = o->sell_steps_t = 0;
+    o->unit_cost_a = o->unit_cost_t = 0.0;
     return HPR_OK;
 }
 
@@ -883,6 +1025,11 @@ static int check_options(hpr_ctx *ctx, const hpr_options *o)
     if (!(o->switch_tol >= 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "switch_tol must be >= 0");
     if (o->halpern != 0 && o->halpern != 1) return fail_arg(ctx, HPR_ERR_ARG, "halpern must be 0 or 1");
     if (o->reflect != 0 && o->reflect != 1) return fail_arg(ctx, HPR_ERR_ARG, "reflect must be 0 or 1");
+    if (o->autotune != 0 && o->autotune != 1) return fail_arg(ctx, HPR_ERR_ARG, "autotune must be 0 or 1");
+    if (o->sell_steps_a < 0 || o->sell_steps_a > 4096 || o->sell_steps_t < 0 || o->sell_steps_t > 4096)
+        return fail_arg(ctx, HPR_ERR_ARG, "sell_steps must be in [0, 4096]");
+    if (!(o->unit_cost_a >= 0.0) || !(o->unit_cost_t >= 0.0) || o->unit_cost_a > 1e9 || o->unit_cost_t > 1e9)
+        return fail_arg(ctx, HPR_ERR_ARG, "unit_cost must be in [0, 1e9]");
     return HPR_OK;
 }
 
@@ -1381,6 +1528,15 @@ int hpr_get_scaling(const hpr_ctx *cctx, double *Dr, double *Dc, double *As_val,
         beta[0] = ctx->beta_b;
         beta[1] = ctx->beta_c;
     }
+    return HPR_OK;
+}
+
+int hpr_get_layout(const hpr_ctx *ctx, int64_t *sell_steps, double *unit_cost, int64_t *units)
+{
+    if (!ctx) return HPR_ERR_ARG;
+    if (sell_steps) { sell_steps[0] = ctx->SA.steps_max; sell_steps[1] = ctx->ST.steps_max; }
+    if (unit_cost) { unit_cost[0] = ctx->SA.unit_cost; unit_cost[1] = ctx->ST.unit_cost; }
+    if (units) { units[0] = ctx->SA.nruns; units[1] = ctx->ST.nruns; }
     return HPR_OK;
 }
 

@@ -44,7 +44,10 @@ class hpr_options(ctypes.Structure):
                 ("trace_iters", ctypes.c_int64), ("use_graph", ctypes.c_int64),
                 ("verbose", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
                 ("precision", ctypes.c_int64), ("switch_tol", ctypes.c_double),
-                ("halpern", ctypes.c_int64), ("reflect", ctypes.c_int64)]
+                ("halpern", ctypes.c_int64), ("reflect", ctypes.c_int64),
+                ("autotune", ctypes.c_int64), ("sell_steps_a", ctypes.c_int64),
+                ("sell_steps_t", ctypes.c_int64), ("unit_cost_a", ctypes.c_double),
+                ("unit_cost_t", ctypes.c_double)]
 
 
 class hpr_info(ctypes.Structure):
@@ -90,6 +93,7 @@ SIGNATURES = {
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                          ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, _D, _I64]),
+    "hpr_get_layout": (ctypes.c_int, [ctypes.c_void_p, _I64, _D, _I64]),
     "hpr_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "hpr_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
@@ -292,6 +296,14 @@ class Solver:
         """(x, y, z, info) of the last solve (e.g. one run through a Batch)."""
         x, y, z, info = hpr_get(self.ctx, self.n, self.m)
         return dict(x=x, y=y, z=z, info=info, status=int(info["status"]))
+
+    def layout(self):
+        """Sliced-ELL layout parameters of A and A^T: dict of (A, A^T) pairs."""
+        st = (ctypes.c_int64 * 2)()
+        uc = (ctypes.c_double * 2)()
+        un = (ctypes.c_int64 * 2)()
+        _check(load().hpr_get_layout(self.ctx, st, uc, un), self.ctx)
+        return dict(sell_steps=tuple(st), unit_cost=tuple(uc), units=tuple(un))
 
     def time_iteration(self, reps=50):
         return hpr_time_iteration(self.ctx, reps)

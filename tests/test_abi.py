@@ -120,3 +120,12 @@ def test_status_strings(lib):
     assert hpr.hpr_status_str(0) == "HPR_OK"
     assert hpr.hpr_status_str(-5) == "HPR_ERR_DEVICE_TIMEOUT"
     assert hpr.hpr_status_str(99) == "HPR_UNKNOWN"
+
+
+@pytest.mark.parametrize("bad", [dict(sell_steps_a=-1), dict(sell_steps_t=5000), dict(unit_cost_t=-2.0),
+                                 dict(autotune=2), dict(halpern=3), dict(reflect=-1), dict(precision=2)])
+def test_invalid_options_rejected(lib, bad):
+    lp = _tiny()
+    with pytest.raises(hpr.HprError) as e:
+        hpr.Solver(lp, **bad)
+    assert e.value.code == hpr.HPR_ERR_ARG
