@@ -105,6 +105,15 @@ typedef struct {
                                  its longest row within this many steps; 0: 40 */
     double unit_cost_a, unit_cost_t;     /* work-unit size of A's / A^T's layout (a group
                                  costlier than this is split into one unit per slice); 0: 64 */
+    int64_t sigma_policy;     /* sigma at a restart where Algorithm 3 computes Delta_x / Delta_y:
+                                 0 (default) that value; 1 (exploration, for training data)
+                                 2^((a-2)/2) times it with a in 0..4 drawn by SplitMix64 from
+                                 policy_seed and the restart count; 2 the same multiplier with
+                                 a = the argmin of the policy network set by hpr_set_policy,
+                                 except after a learned choice whose inner loop saw the KKT
+                                 residual rise above its value at the decision: the next
+                                 restart then keeps Algorithm 3's value (a fallback) */
+    uint64_t policy_seed;
 } hpr_options;
 
 /* Result summary (original, unscaled problem). */
@@ -121,6 +130,8 @@ typedef struct {
     int64_t launches;             /* kernels launched by the solve (graph nodes included) */
     int64_t status;               /* HPR_OK, HPR_MAX_ITER or HPR_TIME_LIMIT */
     int64_t iters_fp32;           /* iterations run in the FP32 form (precision 1) */
+    int64_t policy_decisions;     /* restarts whose sigma the policy network chose */
+    int64_t policy_fallbacks;     /* restarts that fell back to Algorithm 3 (sigma_policy 2) */
 } hpr_info;
 
 /* One evaluation of the restart / termination quantities.  kind: 1 = periodic check,
@@ -130,6 +141,8 @@ typedef struct {
     int64_t k, r, t, kind, cause;
     double sigma, err_p, err_d, err_gap, kkt, pobj, dobj;
     double Rt, R0, sigma_next, Dx, Dy, elapsed_s;
+    int64_t action;               /* sigma multiplier index of a restart (-1: Algorithm 3's) */
+    double sigma_rule;            /* Algorithm 3's sigma at that restart */
 } hpr_check_record;
 
 /* Fills *opt with the defaults above.  Returns HPR_OK or HPR_ERR_ARG (opt NULL). */
@@ -246,6 +259,36 @@ int hpr_batch_solve(hpr_batch *batch, double tol);
  * the fused launches it made; any pointer may be NULL. */
 int hpr_batch_stats(const hpr_batch *batch, double *solve_time_s, int64_t *periods, int64_t *fused_launches);
 void hpr_batch_destroy(hpr_batch *batch);
+
+/* ---- The sigma policy network (no counterpart in the paper).  An MLP with three hidden
+ * layers of 64 ReLU units maps 64 features of the recent check history (for each of the
+ * last 16 checks: log10 err_p, log10 err_d, log10 gap, log10 sigma, each over 8) to five
+ * outputs, the predicted change of log10 KKT after choosing sigma = 2^((a-2)/2) times
+ * Algorithm 3's sigma (a = 0..4) at a restart.  Weights: hpr_mlp_param_count() FP32
+ * values, rows of W[out][in] then biases, layer by layer (W1 64x64, b1, W2 64x64, b2,
+ * W3 64x64, b3, W4 5x64, b4); the kernels compute with their BF16 rounding and FP32
+ * accumulation.  All arrays are HOST arrays owned by the caller; X is n x 64 row-major.
+ * Each returns HPR_OK, HPR_ERR_ARG (NULL array, n outside [1, 2^26], action outside
+ * [0, 5), non-finite input) or HPR_ERR_NOMEM / HPR_ERR_CUDA, detail in hpr_last_error(NULL). */
+int hpr_mlp_param_count(void);
+/* The policy a context uses with sigma_policy = 2: w (hpr_mlp_param_count() FP32 values,
+ * host) is copied; NULL removes it (sigma_policy 2 then behaves as 0). */
+int hpr_set_policy(hpr_ctx *ctx, const float *w);
+/* The 64 features of check record `rec` of the last solve (as the policy sees them at a
+ * restart decided at that check) into out (host, 64 floats). */
+int hpr_policy_features(const hpr_ctx *ctx, int64_t rec, float *out);
+/* Q (n x 5): the outputs for each row of X. */
+int hpr_mlp_infer(const float *w, int64_t n, const float *X, float *Q);
+/* Loss L = mean_i 1/2 (Q(x_i)[act_i] - y_i)^2 and dL/dw (P values, with respect to the
+ * BF16 weights) into grad and *loss. */
+int hpr_mlp_grad(const float *w, int64_t n, const float *X, const int32_t *act, const float *y, float *grad,
+                 double *loss);
+/* Adam (beta 0.9 / 0.999, eps 1e-8, step lr) over `epochs` passes in minibatches of
+ * `batch` samples, the order of each pass drawn from SplitMix64(seed); w is updated in
+ * place (FP32 masters); epoch_loss (epochs values, may be NULL) gets each pass's mean
+ * minibatch loss. */
+int hpr_mlp_train(float *w, int64_t n, const float *X, const int32_t *act, const float *y, int64_t epochs,
+                  int64_t batch, double lr, uint64_t seed, double *epoch_loss);
 
 /* Detail of the last error of ctx (a static string when ctx is NULL). */
 const char *hpr_last_error(const hpr_ctx *ctx);

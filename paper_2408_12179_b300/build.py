@@ -11,7 +11,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "hpr_api.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", "hpr_device.cuh"), os.path.join(ROOT, "include", "hpr.h")]
+DEPS = SRC + [os.path.join(HERE, "csrc", "hpr_device.cuh"), os.path.join(HERE, "csrc", "hpr_mlp.cuh"),
+              os.path.join(ROOT, "include", "hpr.h")]
 LIB = os.path.join(HERE, "libhpr_b300.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

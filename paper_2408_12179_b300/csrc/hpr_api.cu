@@ -16,6 +16,7 @@
 // the batch is captured once as a CUDA graph and replayed.
 #include "hpr.h"
 #include "hpr_device.cuh"
+#include "hpr_mlp.cuh"
 
 #include <cuda_runtime.h>
 
@@ -78,6 +79,10 @@ struct SolveState {
     int64_t iters_1e4 = -1, iters_fp32 = 0;
     bool tracing = false, done = false;
     bool ctl_off = false;                 // batched: the control block already says inactive
+    int64_t policy_decisions = 0, policy_fallbacks = 0;
+    bool policy_watch = false;            // a learned sigma is in use: watch the KKT residual
+    bool policy_suspend = false;          // it rose: the next restart keeps Algorithm 3's sigma
+    double policy_kkt = 0.0;              // KKT residual at the learned decision
     int L = 0;                            // the current period: iterations and whether it
     bool first_r0 = false;                // starts an inner loop (t = 0)
 };
@@ -144,6 +149,8 @@ struct hpr_ctx {
     double power_time = 0.0;
     hpr_info info{};
     SolveState ss;
+    __nv_bfloat16 *policy_wb = nullptr;   // sigma policy network (BF16), its input and output
+    float *policy_w32 = nullptr, *policy_x = nullptr, *policy_q = nullptr;
     bool batched = false;         // owned by a batch: solved only through hpr_batch_solve
     std::vector<hpr_check_record> checks;
     std::string err;
@@ -347,7 +354,8 @@ void free_all(hpr_ctx *c)
                    c->unperm, c->Dr, c->Dc, c->wr, c->wc, c->b_s, c->c_s,
                    c->l_s, c->u_s, c->l_o, c->u_o, c->x, c->x0, c->xhat, c->xbar,
                    c->zbar, c->dx, c->y, c->y0, c->ybar, c->dy, c->xo, c->yo, c->zo,
-                   c->partials, c->scal, c->ctl, c->pctl, c->trace};
+                   c->partials, c->scal, c->ctl, c->pctl, c->trace, c->policy_wb, c->policy_w32,
+                   c->policy_x, c->policy_q};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->scal_h) cudaFreeHost(c->scal_h);
@@ -1007,6 +1015,8 @@ int hpr_default_options(hpr_options *o)
     o->autotune = 0;
     o->sell_steps_a = o->sell_steps_t = 0;
     o->unit_cost_a = o->unit_cost_t = 0.0;
+    o->sigma_policy = 0;
+    o->policy_seed = 0x5167;
     return HPR_OK;
 }
 
@@ -1026,6 +1036,7 @@ static int check_options(hpr_ctx *ctx, const hpr_options *o)
     if (o->halpern != 0 && o->halpern != 1) return fail_arg(ctx, HPR_ERR_ARG, "halpern must be 0 or 1");
     if (o->reflect != 0 && o->reflect != 1) return fail_arg(ctx, HPR_ERR_ARG, "reflect must be 0 or 1");
     if (o->autotune != 0 && o->autotune != 1) return fail_arg(ctx, HPR_ERR_ARG, "autotune must be 0 or 1");
+    if (o->sigma_policy < 0 || o->sigma_policy > 2) return fail_arg(ctx, HPR_ERR_ARG, "sigma_policy must be 0, 1 or 2");
     if (o->sell_steps_a < 0 || o->sell_steps_a > 4096 || o->sell_steps_t < 0 || o->sell_steps_t > 4096)
         return fail_arg(ctx, HPR_ERR_ARG, "sell_steps must be in [0, 4096]");
     if (!(o->unit_cost_a >= 0.0) || !(o->unit_cost_t >= 0.0) || o->unit_cost_a > 1e9 || o->unit_cost_t > 1e9)
@@ -1174,6 +1185,52 @@ namespace {
 // synchronisation, period_after (termination, restart and sigma decisions of the check)
 // -- and solve_finish (back-map, summary).  hpr_solve runs one context through them;
 // hpr_batch_solve runs many in lock step with fused kernels.
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the next output of the sequence at `state`
+uint64_t splitmix64_next(uint64_t &state)
+{
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// The policy network's input at check record `rec`: the last 16 periodic checks up to and
+// including it (the oldest repeated when fewer exist), each as log10 err_p, log10 err_d,
+// log10 gap (floored at 1e-16) and log10 sigma, all divided by 8.
+void policy_features(const std::vector<hpr_check_record> &recs, int64_t rec, float *out)
+{
+    std::vector<const hpr_check_record *> hist;
+    for (int64_t i = rec; i >= 0 && hist.size() < 16; --i)
+        if (recs[(size_t)i].kind & 1) hist.push_back(&recs[(size_t)i]);
+    if (hist.empty()) hist.push_back(&recs[(size_t)rec]);
+    while (hist.size() < 16) hist.push_back(hist.back());
+    for (int j = 0; j < 16; ++j) {
+        const hpr_check_record *c = hist[(size_t)(15 - j)];   // oldest first
+        out[4 * j + 0] = (float)(std::log10(std::max(c->err_p, 1e-16)) / 8.0);
+        out[4 * j + 1] = (float)(std::log10(std::max(c->err_d, 1e-16)) / 8.0);
+        out[4 * j + 2] = (float)(std::log10(std::max(c->err_gap, 1e-16)) / 8.0);
+        out[4 * j + 3] = (float)(std::log10(std::max(c->sigma, 1e-300)) / 8.0);
+    }
+}
+
+// action of the policy network at the last check record: argmin of its five outputs
+int policy_choose(hpr_ctx *ctx, int *action)
+{
+    float x[hprmlp::IN], q[hprmlp::OUT];
+    policy_features(ctx->checks, (int64_t)ctx->checks.size() - 1, x);
+    CK(cudaMemcpyAsync(ctx->policy_x, x, sizeof x, cudaMemcpyHostToDevice, ctx->stream));
+    hprmlp::k_infer<<<1, hprmlp::TPB, 0, ctx->stream>>>(ctx->policy_wb, ctx->policy_x, 1, ctx->policy_q);
+    CKL();
+    ctx->launches += 1;
+    CK(cudaMemcpyAsync(q, ctx->policy_q, sizeof q, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int best = 0;
+    for (int a = 1; a < hprmlp::OUT; ++a)
+        if (q[a] < q[best]) best = a;
+    *action = best;
+    return HPR_OK;
+}
 
 int solve_begin(hpr_ctx *ctx, double tol)
 {
@@ -1339,7 +1396,7 @@ int period_after(hpr_ctx *ctx, double elapsed)
         hpr_check_record rec{};
         rec.k = S.k; rec.r = S.r; rec.t = 0; rec.kind = 2; rec.cause = 0;
         rec.sigma = S.sigma; rec.Rt = S.R0; rec.R0 = S.R0; rec.sigma_next = S.sigma;
-        rec.elapsed_s = elapsed;
+        rec.elapsed_s = elapsed; rec.action = -1; rec.sigma_rule = S.sigma;
         ctx->checks.push_back(rec);
     }
     const bool is_r0 = (tl == 0);
@@ -1379,16 +1436,24 @@ int period_after(hpr_ctx *ctx, double elapsed)
         S.Rprev = Rt;
         restart = cause != 0;
     }
+    bool rule_sigma = false;                  // sigma_next is Delta_x / Delta_y
     if (restart) {
         // Algorithm 3 with eq. (sigma_T1!=0)
         Dx = std::sqrt(S1[Q_XX0]);
         Dy = std::sqrt(lambda) * std::sqrt(S1[Q_YY0]);
         const double ratio = errd / errp;
-        if (o.sigma_update && Dx > 1e-16 && Dx < 1e12 && Dy > 1e-16 && Dy < 1e12 &&
-            errp > 0.0 && ratio > 1e-8 && ratio < 1e8)
+        rule_sigma = o.sigma_update && Dx > 1e-16 && Dx < 1e12 && Dy > 1e-16 && Dy < 1e12 &&
+                     errp > 0.0 && ratio > 1e-8 && ratio < 1e8;
+        if (rule_sigma)
             sigma_next = Dx / Dy;
         else
             sigma_next = o.sigma_update ? 1.0 : S.sigma;
+    }
+    // a learned sigma is watched until the next restart: a KKT residual above its value at
+    // the decision sends the next restart back to Algorithm 3
+    if (S.policy_watch && kkt > S.policy_kkt) {
+        S.policy_suspend = true;
+        S.policy_watch = false;
     }
     {
         hpr_check_record rec{};
@@ -1396,7 +1461,31 @@ int period_after(hpr_ctx *ctx, double elapsed)
         rec.sigma = S.sigma; rec.err_p = errp; rec.err_d = errd; rec.err_gap = gap; rec.kkt = kkt;
         rec.pobj = pobj; rec.dobj = dobj; rec.Rt = Rt; rec.R0 = S.R0; rec.sigma_next = sigma_next;
         rec.Dx = Dx; rec.Dy = Dy; rec.elapsed_s = elapsed;
+        rec.action = -1; rec.sigma_rule = sigma_next;
         ctx->checks.push_back(rec);
+    }
+    if (restart) S.policy_watch = false;      // a new inner loop: a new decision below
+    if (restart && rule_sigma && o.sigma_policy != 0) {
+        int action = -1;
+        if (o.sigma_policy == 1) {
+            uint64_t st64 = o.policy_seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(S.r + 1));
+            action = (int)(splitmix64_next(st64) % (uint64_t)hprmlp::OUT);
+        } else if (ctx->policy_wb) {
+            if (S.policy_suspend) {
+                S.policy_suspend = false;
+                S.policy_fallbacks++;
+            } else {
+                if ((st = policy_choose(ctx, &action))) return st;
+                S.policy_decisions++;
+                S.policy_watch = true;
+                S.policy_kkt = kkt;
+            }
+        }
+        if (action >= 0) {
+            sigma_next *= std::exp2(0.5 * (double)(action - 2));
+            ctx->checks.back().action = action;
+            ctx->checks.back().sigma_next = sigma_next;
+        }
     }
     if (o.verbose)
         fprintf(stderr, "hpr k=%lld r=%lld t=%lld sigma=%.3e kkt=%.3e (p %.2e d %.2e g %.2e) R=%.3e cause=%d %.3fs\n",
@@ -1468,6 +1557,8 @@ int solve_finish(hpr_ctx *ctx)
     I.iters = S.k; I.restarts = S.r; I.power_iters = ctx->power_iters;
     I.n_checks = (int64_t)ctx->checks.size(); I.launches = ctx->launches; I.status = S.status;
     I.iters_fp32 = S.iters_fp32;
+    I.policy_decisions = S.policy_decisions;
+    I.policy_fallbacks = S.policy_fallbacks;
     ctx->solved = true;
     return S.status;
 }
@@ -1998,6 +2089,208 @@ void hpr_batch_destroy(hpr_batch *b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_free(b);
     delete b;
+}
+
+}  // extern "C"
+
+
+// ====================================================================== sigma policy network
+namespace {
+
+struct MlpBuffers {
+    float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr, *gpart = nullptr, *X = nullptr, *y = nullptr;
+    __nv_bfloat16 *wb = nullptr;
+    double *lpart = nullptr, *loss = nullptr;
+    int *act = nullptr, *idx = nullptr;
+    int max_ctas = 0;
+    ~MlpBuffers()
+    {
+        void *p[] = {w, m, v, g, gpart, X, y, wb, lpart, loss, act, idx};
+        for (void *q : p)
+            if (q) cudaFree(q);
+    }
+};
+
+int mlp_check_data(int64_t n, const float *X, const int32_t *act, const float *y)
+{
+    if (n < 1 || n > ((int64_t)1 << 26) || !X || (act && !y) || (!act && y)) return HPR_ERR_ARG;
+    for (int64_t i = 0; i < n * hprmlp::IN; ++i)
+        if (!std::isfinite(X[i])) return HPR_ERR_ARG;
+    if (act)
+        for (int64_t i = 0; i < n; ++i)
+            if (act[i] < 0 || act[i] >= hprmlp::OUT || !std::isfinite(y[i])) return HPR_ERR_ARG;
+    return HPR_OK;
+}
+
+// upload weights (and data) and make the BF16 copy
+int mlp_setup(MlpBuffers &B, const float *w, int64_t n, const float *X, const int32_t *act, const float *y,
+              int64_t batch)
+{
+    using namespace hprmlp;
+    B.max_ctas = (int)std::min<int64_t>(592, std::max<int64_t>(1, (batch + 7) / 8));
+    if (cudaMalloc((void **)&B.w, sizeof(float) * P) || cudaMalloc((void **)&B.m, sizeof(float) * P) ||
+        cudaMalloc((void **)&B.v, sizeof(float) * P) || cudaMalloc((void **)&B.g, sizeof(float) * P) ||
+        cudaMalloc((void **)&B.wb, sizeof(__nv_bfloat16) * P) ||
+        cudaMalloc((void **)&B.gpart, sizeof(float) * (size_t)P * B.max_ctas) ||
+        cudaMalloc((void **)&B.lpart, sizeof(double) * B.max_ctas) || cudaMalloc((void **)&B.loss, sizeof(double) * 2) ||
+        cudaMalloc((void **)&B.X, sizeof(float) * (size_t)n * IN) || cudaMalloc((void **)&B.idx, sizeof(int) * (size_t)n))
+        return HPR_ERR_NOMEM;
+    if (act && (cudaMalloc((void **)&B.act, sizeof(int) * (size_t)n) || cudaMalloc((void **)&B.y, sizeof(float) * (size_t)n)))
+        return HPR_ERR_NOMEM;
+    if (cudaMemcpy(B.w, w, sizeof(float) * P, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(B.X, X, sizeof(float) * (size_t)n * IN, cudaMemcpyHostToDevice) ||
+        cudaMemset(B.m, 0, sizeof(float) * P) || cudaMemset(B.v, 0, sizeof(float) * P))
+        return HPR_ERR_CUDA;
+    if (act && (cudaMemcpy(B.act, act, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice) ||
+                cudaMemcpy(B.y, y, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice)))
+        return HPR_ERR_CUDA;
+    if (cudaFuncSetAttribute(k_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRAD_SMEM)) return HPR_ERR_CUDA;
+    k_to_bf16<<<26, 512>>>(B.w, B.wb);
+    return cudaGetLastError() == cudaSuccess ? HPR_OK : HPR_ERR_CUDA;
+}
+
+// mean loss and gradient over samples idx[0 .. count) (idx NULL: the first count)
+int mlp_grad_pass(MlpBuffers &B, const int *idx, int64_t count, double *loss_dst)
+{
+    using namespace hprmlp;
+    const int ctas = (int)std::min<int64_t>(B.max_ctas, count);
+    const int chunk = (int)((count + ctas - 1) / ctas);
+    const int used = (int)((count + chunk - 1) / chunk);
+    k_grad<<<used, TPB, GRAD_SMEM>>>(B.wb, B.X, B.act, B.y, idx, (int)count, chunk, B.gpart, B.lpart);
+    k_reduce_grad<<<26, 512>>>(B.gpart, B.lpart, used, 1.0 / (double)count, B.g, loss_dst);
+    return cudaGetLastError() == cudaSuccess ? HPR_OK : HPR_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hpr_mlp_param_count(void) { return hprmlp::P; }
+
+int hpr_set_policy(hpr_ctx *ctx, const float *w)
+{
+    if (!ctx) return HPR_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (!w) {
+        if (ctx->policy_wb) cudaFree(ctx->policy_wb);
+        ctx->policy_wb = nullptr;
+        return HPR_OK;
+    }
+    for (int p = 0; p < hprmlp::P; ++p)
+        if (!std::isfinite(w[p])) return fail_arg(ctx, HPR_ERR_ARG, "hpr_set_policy: non-finite weight");
+    if (!ctx->policy_wb) DALLOC(ctx->policy_wb, hprmlp::P);
+    if (!ctx->policy_w32) DALLOC(ctx->policy_w32, hprmlp::P);
+    if (!ctx->policy_x) DALLOC(ctx->policy_x, hprmlp::IN);
+    if (!ctx->policy_q) DALLOC(ctx->policy_q, hprmlp::OUT);
+    CK(cudaMemcpyAsync(ctx->policy_w32, w, sizeof(float) * hprmlp::P, cudaMemcpyHostToDevice, ctx->stream));
+    hprmlp::k_to_bf16<<<26, 512, 0, ctx->stream>>>(ctx->policy_w32, ctx->policy_wb);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->stream));
+    return HPR_OK;
+}
+
+int hpr_policy_features(const hpr_ctx *ctx, int64_t rec, float *out)
+{
+    if (!ctx || !out) return HPR_ERR_ARG;
+    if (rec < 0 || rec >= (int64_t)ctx->checks.size())
+        return fail_arg(const_cast<hpr_ctx *>(ctx), HPR_ERR_ARG, "hpr_policy_features: no such check record");
+    policy_features(ctx->checks, rec, out);
+    return HPR_OK;
+}
+
+int hpr_mlp_infer(const float *w, int64_t n, const float *X, float *Q)
+{
+    if (!w || !Q || mlp_check_data(n, X, nullptr, nullptr)) {
+        g_static_err = "hpr_mlp_infer: NULL array, n outside [1, 2^26] or non-finite input";
+        return HPR_ERR_ARG;
+    }
+    MlpBuffers B;
+    int st = mlp_setup(B, w, n, X, nullptr, nullptr, 1);
+    if (st) { g_static_err = "hpr_mlp_infer: device setup failed"; return st; }
+    float *dQ = nullptr;
+    if (cudaMalloc((void **)&dQ, sizeof(float) * (size_t)n * hprmlp::OUT)) return HPR_ERR_NOMEM;
+    hprmlp::k_infer<<<(int)std::min<int64_t>(n, 4096), hprmlp::TPB>>>(B.wb, B.X, (int)n, dQ);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(Q, dQ, sizeof(float) * (size_t)n * hprmlp::OUT, cudaMemcpyDeviceToHost);
+    cudaFree(dQ);
+    if (e != cudaSuccess) { g_static_err = "hpr_mlp_infer: CUDA error"; return HPR_ERR_CUDA; }
+    return HPR_OK;
+}
+
+int hpr_mlp_grad(const float *w, int64_t n, const float *X, const int32_t *act, const float *y, float *grad,
+                 double *loss)
+{
+    if (!w || !grad || !act || mlp_check_data(n, X, act, y)) {
+        g_static_err = "hpr_mlp_grad: NULL array, n outside [1, 2^26], action outside [0, 5) or non-finite input";
+        return HPR_ERR_ARG;
+    }
+    MlpBuffers B;
+    int st = mlp_setup(B, w, n, X, act, y, n);
+    if (st) { g_static_err = "hpr_mlp_grad: device setup failed"; return st; }
+    if ((st = mlp_grad_pass(B, nullptr, n, B.loss))) return st;
+    if (cudaMemcpy(grad, B.g, sizeof(float) * hprmlp::P, cudaMemcpyDeviceToHost) != cudaSuccess) return HPR_ERR_CUDA;
+    if (loss && cudaMemcpy(loss, B.loss, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return HPR_ERR_CUDA;
+    return HPR_OK;
+}
+
+int hpr_mlp_train(float *w, int64_t n, const float *X, const int32_t *act, const float *y, int64_t epochs,
+                  int64_t batch, double lr, uint64_t seed, double *epoch_loss)
+{
+    if (!w || !act || mlp_check_data(n, X, act, y) || epochs < 0 || epochs > 100000 || batch < 1 ||
+        !(lr > 0.0) || !(lr < 1.0)) {
+        g_static_err = "hpr_mlp_train: bad arguments (NULL array, n outside [1, 2^26], action outside [0, 5), "
+                       "non-finite input, epochs outside [0, 1e5], batch < 1 or lr outside (0, 1))";
+        return HPR_ERR_ARG;
+    }
+    batch = std::min(batch, n);
+    MlpBuffers B;
+    int st = mlp_setup(B, w, n, X, act, y, batch);
+    if (st) { g_static_err = "hpr_mlp_train: device setup failed"; return st; }
+    const int64_t steps_per_epoch = (n + batch - 1) / batch;
+    double *hist = nullptr;
+    if (cudaMalloc((void **)&hist, sizeof(double) * (size_t)std::max<int64_t>(1, epochs * steps_per_epoch)))
+        return HPR_ERR_NOMEM;
+    std::vector<int> perm((size_t)n);
+    uint64_t rng = seed;
+    int64_t t = 0;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int64_t ep = 0; ep < epochs && st == HPR_OK; ++ep) {
+        // Fisher-Yates with SplitMix64 draws: a fixed sample order per (seed, epoch)
+        for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = (int)i;
+        for (int64_t i = n - 1; i > 0; --i) {
+            const int64_t r = (int64_t)(splitmix64_next(rng) % (uint64_t)(i + 1));
+            std::swap(perm[(size_t)i], perm[(size_t)r]);
+        }
+        if (cudaMemcpy(B.idx, perm.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            st = HPR_ERR_CUDA;
+            break;
+        }
+        for (int64_t s0 = 0; s0 < n && st == HPR_OK; s0 += batch) {
+            const int64_t cnt = std::min(batch, n - s0);
+            st = mlp_grad_pass(B, B.idx + s0, cnt, hist + t);
+            ++t;
+            const float c1 = 1.f - std::pow(b1, (float)t), c2 = 1.f - std::pow(b2, (float)t);
+            hprmlp::k_adam<<<26, 512>>>(B.w, B.m, B.v, B.g, (float)lr, b1, b2, eps, c1, c2, B.wb);
+            if (st == HPR_OK && cudaGetLastError() != cudaSuccess) st = HPR_ERR_CUDA;
+        }
+    }
+    if (st == HPR_OK && cudaMemcpy(w, B.w, sizeof(float) * hprmlp::P, cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = HPR_ERR_CUDA;
+    if (st == HPR_OK && epoch_loss && epochs > 0) {
+        std::vector<double> h((size_t)(epochs * steps_per_epoch));
+        if (cudaMemcpy(h.data(), hist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            st = HPR_ERR_CUDA;
+        } else {
+            for (int64_t ep = 0; ep < epochs; ++ep) {
+                double sum = 0.0;
+                for (int64_t k = 0; k < steps_per_epoch; ++k) sum += h[(size_t)(ep * steps_per_epoch + k)];
+                epoch_loss[ep] = sum / (double)steps_per_epoch;
+            }
+        }
+    }
+    cudaFree(hist);
+    if (st) g_static_err = "hpr_mlp_train: CUDA error";
+    return st;
 }
 
 }  // extern "C"

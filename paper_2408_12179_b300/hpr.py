@@ -47,7 +47,8 @@ class hpr_options(ctypes.Structure):
                 ("halpern", ctypes.c_int64), ("reflect", ctypes.c_int64),
                 ("autotune", ctypes.c_int64), ("sell_steps_a", ctypes.c_int64),
                 ("sell_steps_t", ctypes.c_int64), ("unit_cost_a", ctypes.c_double),
-                ("unit_cost_t", ctypes.c_double)]
+                ("unit_cost_t", ctypes.c_double), ("sigma_policy", ctypes.c_int64),
+                ("policy_seed", ctypes.c_uint64)]
 
 
 class hpr_info(ctypes.Structure):
@@ -60,7 +61,8 @@ class hpr_info(ctypes.Structure):
                 ("iters", ctypes.c_int64), ("restarts", ctypes.c_int64),
                 ("power_iters", ctypes.c_int64), ("n_checks", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("status", ctypes.c_int64),
-                ("iters_fp32", ctypes.c_int64)]
+                ("iters_fp32", ctypes.c_int64),
+                ("policy_decisions", ctypes.c_int64), ("policy_fallbacks", ctypes.c_int64)]
 
 
 class hpr_check_record(ctypes.Structure):
@@ -70,7 +72,8 @@ class hpr_check_record(ctypes.Structure):
                 ("err_d", ctypes.c_double), ("err_gap", ctypes.c_double),
                 ("kkt", ctypes.c_double), ("pobj", ctypes.c_double), ("dobj", ctypes.c_double),
                 ("Rt", ctypes.c_double), ("R0", ctypes.c_double), ("sigma_next", ctypes.c_double),
-                ("Dx", ctypes.c_double), ("Dy", ctypes.c_double), ("elapsed_s", ctypes.c_double)]
+                ("Dx", ctypes.c_double), ("Dy", ctypes.c_double), ("elapsed_s", ctypes.c_double),
+                ("action", ctypes.c_int64), ("sigma_rule", ctypes.c_double)]
 
 
 # every symbol the header declares, with (restype, argtypes)
@@ -99,6 +102,15 @@ SIGNATURES = {
     "hpr_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "hpr_batch_stats": (ctypes.c_int, [ctypes.c_void_p, _D, _I64, _I64]),
     "hpr_batch_destroy": (None, [ctypes.c_void_p]),
+    "hpr_set_policy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hpr_policy_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "hpr_mlp_param_count": (ctypes.c_int, []),
+    "hpr_mlp_infer": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    "hpr_mlp_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, _D]),
+    "hpr_mlp_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                     ctypes.c_uint64, ctypes.c_void_p]),
     "hpr_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hpr_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "hpr_destroy": (None, [ctypes.c_void_p]),
@@ -257,6 +269,46 @@ def hpr_power_noalloc(m, n, A_ptrs, At_ptrs, seed, max_iter, tol, u_ptr, s_ptr, 
     return lam.value, it.value
 
 
+def _f32(a, cols=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if cols is not None:
+        a = a.reshape(-1, cols)
+    return a
+
+
+def mlp_param_count():
+    return int(load().hpr_mlp_param_count())
+
+
+def mlp_infer(w, X):
+    """Outputs (n x 5) of the sigma policy network for the rows of X (n x 64)."""
+    w, X = _f32(w), _f32(X, 64)
+    Q = np.empty((X.shape[0], 5), np.float32)
+    _check(load().hpr_mlp_infer(w.ctypes.data, X.shape[0], X.ctypes.data, Q.ctypes.data), None)
+    return Q
+
+
+def mlp_grad(w, X, act, y):
+    """(loss, gradient) of the network's regression loss on the GPU."""
+    w, X, y = _f32(w), _f32(X, 64), _f32(y)
+    act = np.ascontiguousarray(act, dtype=np.int32)
+    g = np.empty(w.size, np.float32)
+    loss = ctypes.c_double()
+    _check(load().hpr_mlp_grad(w.ctypes.data, X.shape[0], X.ctypes.data, act.ctypes.data, y.ctypes.data,
+                               g.ctypes.data, ctypes.byref(loss)), None)
+    return loss.value, g
+
+
+def mlp_train(w, X, act, y, epochs=50, batch=256, lr=1e-3, seed=1):
+    """Trains on the GPU; returns (weights, per-epoch losses)."""
+    w, X, y = _f32(w).copy(), _f32(X, 64), _f32(y)
+    act = np.ascontiguousarray(act, dtype=np.int32)
+    hist = np.zeros(max(int(epochs), 1))
+    _check(load().hpr_mlp_train(w.ctypes.data, X.shape[0], X.ctypes.data, act.ctypes.data, y.ctypes.data,
+                                int(epochs), int(batch), float(lr), int(seed), hist.ctypes.data), None)
+    return w, hist[:int(epochs)]
+
+
 def hpr_destroy(ctx):
     if ctx is not None and ctx.value:
         load().hpr_destroy(ctx)
@@ -296,6 +348,19 @@ class Solver:
         """(x, y, z, info) of the last solve (e.g. one run through a Batch)."""
         x, y, z, info = hpr_get(self.ctx, self.n, self.m)
         return dict(x=x, y=y, z=z, info=info, status=int(info["status"]))
+
+    def set_policy(self, w):
+        """Policy network weights for sigma_policy = 2 (None removes them)."""
+        if w is None:
+            _check(load().hpr_set_policy(self.ctx, None), self.ctx)
+            return
+        self._policy_w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(load().hpr_set_policy(self.ctx, self._policy_w.ctypes.data), self.ctx)
+
+    def policy_features(self, rec):
+        out = np.empty(64, np.float32)
+        _check(load().hpr_policy_features(self.ctx, int(rec), out.ctypes.data), self.ctx)
+        return out
 
     def layout(self):
         """Sliced-ELL layout parameters of A and A^T: dict of (A, A^T) pairs."""

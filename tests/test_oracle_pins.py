@@ -500,3 +500,58 @@ def test_mcf_small_vs_highs(orc):
                   bounds=[(0, None)] * lp.n, method="highs")
     assert res.status == 0
     assert abs(ind["pobj"] - res.fun) <= 1e-7 * abs(res.fun)
+
+
+# ------------------------------------------------------------------ sigma policy network oracle
+
+def _mlp_data(seed, n=40):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n, 64)), rng.integers(0, 5, n), rng.standard_normal(n)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    """The chain-rule gradient equals central differences of the loss (FP64 weights, no
+    BF16 rounding) on 200 random coordinates, every layer included."""
+    from oracle import mlp
+    X, a, y = _mlp_data(1)
+    w = mlp.init(3).astype(np.float64)
+    L, g = mlp.loss_grad(w, X, a, y, bf16=False)
+    rng = np.random.default_rng(5)
+    coords = np.concatenate([rng.choice(mlp.P, 192, replace=False),
+                             [0, 4096, 4160, 8256, 8320, 12416, 12480, 12800]])
+    h = 1e-6
+    for c in coords:
+        wp, wm = w.copy(), w.copy()
+        wp[c] += h
+        wm[c] -= h
+        fd = (mlp.loss_grad(wp, X, a, y, bf16=False)[0] - mlp.loss_grad(wm, X, a, y, bf16=False)[0]) / (2 * h)
+        assert abs(fd - g[c]) <= 1e-6 * (1 + abs(fd)), (c, fd, g[c])
+
+
+def test_mlp_closed_form_with_only_output_bias():
+    """All weights 0 but b4: q = b4 for every input, L = mean 1/2 (b4[a] - y)^2, dL/db4[o]
+    = mean over samples of [a = o] (b4[o] - y), every other gradient 0."""
+    from oracle import mlp
+    X, a, y = _mlp_data(2)
+    w = np.zeros(mlp.P)
+    b4 = np.array([0.5, -1.0, 2.0, 0.25, -0.75])
+    w[-5:] = b4
+    L, g = mlp.loss_grad(w, X, a, y, bf16=False)
+    assert L == pytest.approx(0.5 * np.mean((b4[a] - y) ** 2), rel=1e-15)
+    want = np.array([np.sum((b4[o] - y)[a == o]) for o in range(5)]) / len(y)
+    assert np.allclose(g[-5:], want, rtol=1e-14, atol=1e-16)
+    assert not np.any(g[:-5])
+
+
+def test_bf16_rounding_is_nearest_even():
+    """BF16 keeps the top 16 bits of the FP32 pattern, rounding to nearest, ties to even."""
+    from oracle import mlp
+    one = np.float32(1.0)
+    ulp = 2.0 ** -7                                    # BF16 spacing at 1
+    cases = {1.0: 1.0, 1.0 + ulp / 2: 1.0, 1.0 + 3 * ulp / 2: 1.0 + 2 * ulp,
+             1.0 + ulp / 2 + 2.0 ** -20: 1.0 + ulp, -(1.0 + 3 * ulp / 2): -(1.0 + 2 * ulp),
+             3.0e38: 226 * 2.0 ** 120}                 # 3e38 / 2^120 = 225.7: the upper neighbour
+    for x, want in cases.items():
+        got = mlp.bf16_round(np.array([x], np.float32))[0]
+        assert got == pytest.approx(want, rel=1e-7), (x, got, want)
+    assert mlp.bf16_round(np.array([one], np.float32))[0] == 1.0
