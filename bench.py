@@ -168,11 +168,16 @@ def workload(args):
 
     if args.workload == "mcf":
         return lpgen.mcf_lp(args.seed, nodes=max(2, int(round(1_000_000 * args.scale))))
+    if args.workload == "qap":
+        return lpgen.qap_lp(args.seed, args.qap_n)
     return lpgen.planted_medium(args.seed, args.scale)
 
 
 def config_dict(args, lp):
-    if args.workload == "mcf":
+    if args.workload == "qap":
+        name = (f"QAP LP, Adams-Johnson linearisation, random flows and grid distances, N={args.qap_n} "
+                f"(m={lp.m}, n={lp.n}, nnz={lp.nnz}, seed {args.seed})")
+    elif args.workload == "mcf":
         name = (f"min-cost multicommodity flow LP (random geometric 8-NN digraph, 4 commodities; "
                 f"m={lp.m}, m1={lp.m1}, n={lp.n}, nnz={lp.nnz}, seed {args.seed})")
     else:
@@ -502,11 +507,13 @@ def main():
                     help="0: FP64; 1: FP32 form, then FP64 below KKT 1e-5")
     ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true",
                     help="also time one plain FP64 solve and report it beside the chosen form")
-    ap.add_argument("--workload", choices=["medium", "mcf", "batch"], default="medium",
+    ap.add_argument("--workload", choices=["medium", "mcf", "batch", "qap"], default="medium",
                     help="medium sparse planted LP (default), the min-cost multicommodity flow LP "
                          "(1M nodes at scale 1), or a batch of uneven planted LPs solved in one "
                          "batched run (m log-uniform in [500, 50000 * scale])")
     ap.add_argument("--count", type=int, default=512, help="LPs in the batch workload")
+    ap.add_argument("--qap-n", dest="qap_n", type=int, default=30,
+                    help="QAP workload: N (N^4 + N^2 variables)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the sliced-ELL layouts by timing candidates at creation (batch workload: "
                          "once per size bucket of nnz, reused for the bucket's other LPs)")

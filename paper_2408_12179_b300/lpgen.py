@@ -320,6 +320,67 @@ def mcf_lp(seed: int, nodes: int = 1_000_000, k_out: int = 8, commodities: int =
     return LP(A1, A2, b1, b2, c, np.zeros(n), np.full(n, np.inf), name=f"mcf-{seed}-{nodes}")
 
 
+def qap_matrices(seed: int, N: int):
+    """Random QAP data: flows a (symmetric, integers 0..9, zero diagonal) and distances b
+    (Manhattan distances between N distinct points of an N x N grid)."""
+    rng = np.random.default_rng([0x0A9, seed])
+    f = rng.integers(0, 10, (N, N)).astype(np.float64)
+    a = np.triu(f, 1)
+    a = a + a.T
+    cells = rng.choice(N * N, N, replace=False)
+    px, py = cells // N, cells % N
+    b = (np.abs(px[:, None] - px[None, :]) + np.abs(py[:, None] - py[None, :])).astype(np.float64)
+    return a, b
+
+
+def qap_lp(seed: int, N: int) -> LP:
+    """Adams-Johnson linearisation of the QAP min sum a_ik b_jl x_ij x_kl, in the form the
+    paper prints for its QAP experiment: variables x_kl (N^2, in [0, 1]) then s_ijkl
+    (N^4, >= 0, index ((i N + j) N + k) N + l); equality rows sum_i s_ijkl = x_kl (j, k, l),
+    sum_j s_ijkl = x_kl (i, k, l), s_ijkl = s_klij for each unordered pair
+    (i, j) != (k, l), sum_j x_ij = 1 (i) and sum_i x_ij = 1 (j); cost a_ik b_jl on s_ijkl.
+    The flow and distance matrices are random (qap_matrices), not QAPLIB's."""
+    a, b = qap_matrices(seed, N)
+    N2, N4 = N * N, N ** 4
+    i, j, k, l = (v.ravel() for v in np.meshgrid(*(np.arange(N),) * 4, indexing="ij"))
+    sv = N2 + ((i * N + j) * N + k) * N + l
+    xkl = k * N + l
+    rows, cols, vals = [], [], []
+    # sum_i s_ijkl - x_kl = 0, one row per (j, k, l)
+    r1 = (j * N + k) * N + l
+    rows += [r1, np.arange(N ** 3)]
+    cols += [sv, (np.arange(N ** 3) % N2)]
+    vals += [np.ones(N4), -np.ones(N ** 3)]
+    # sum_j s_ijkl - x_kl = 0, one row per (i, k, l)
+    r2 = N ** 3 + (i * N + k) * N + l
+    rows += [r2, N ** 3 + np.arange(N ** 3)]
+    cols += [sv, (np.arange(N ** 3) % N2)]
+    vals += [np.ones(N4), -np.ones(N ** 3)]
+    # s_ijkl - s_klij = 0 for (i, j) < (k, l)
+    p_ij, p_kl = i * N + j, k * N + l
+    keep = p_ij < p_kl
+    nsym = int(keep.sum())
+    r3 = 2 * N ** 3 + np.arange(nsym)
+    rows += [r3, r3]
+    cols += [sv[keep], N2 + ((k[keep] * N + l[keep]) * N + i[keep]) * N + j[keep]]
+    vals += [np.ones(nsym), -np.ones(nsym)]
+    # assignment rows
+    base = 2 * N ** 3 + nsym
+    ii, jj = np.divmod(np.arange(N2), N)
+    rows += [base + ii, base + N + jj]
+    cols += [np.arange(N2), np.arange(N2)]
+    vals += [np.ones(N2), np.ones(N2)]
+    m = base + 2 * N
+    n = N2 + N4
+    A1 = _canonical(sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(m, n)))
+    A2 = _canonical(sp.csr_matrix((0, n)))
+    b1 = np.concatenate([np.zeros(2 * N ** 3 + nsym), np.ones(2 * N)])
+    c = np.concatenate([np.zeros(N2), a[i, k] * b[j, l]])
+    lo = np.zeros(n)
+    up = np.concatenate([np.ones(N2), np.full(N4, np.inf)])
+    return LP(A1, A2, b1, np.zeros(0), c, lo, up, name=f"qap-{seed}-N{N}")
+
+
 def splitmix64_uniform(seed: int, count: int) -> np.ndarray:
     """Reference values of the counter-based generator used by both solvers for the
     power-method start vector (SplitMix64, Steele, Lea & Flood, OOPSLA 2014): the i-th

@@ -555,3 +555,40 @@ def test_bf16_rounding_is_nearest_even():
         got = mlp.bf16_round(np.array([x], np.float32))[0]
         assert got == pytest.approx(want, rel=1e-7), (x, got, want)
     assert mlp.bf16_round(np.array([one], np.float32))[0] == 1.0
+
+
+# ------------------------------------------------------------------ QAP (Adams-Johnson) workload
+
+def _perm_point(N, perm):
+    """The LP point of an assignment: x_ij = [perm(i) = j], s_ijkl = x_ij x_kl."""
+    X = np.zeros((N, N))
+    X[np.arange(N), perm] = 1.0
+    S = np.einsum("ij,kl->ijkl", X, X)
+    return np.concatenate([X.ravel(), S.ravel()])
+
+
+@pytest.mark.parametrize("N", [4, 5])
+def test_qap_lp_relaxes_the_qap(orc, N):
+    """Every assignment, lifted by s_ijkl = x_ij x_kl, satisfies the linearisation's rows
+    and costs sum a_ik b_perm(i)perm(k); the LP optimum found by the oracle matches HiGHS
+    and lies below the best assignment (brute force over all N! of them)."""
+    lp = lpgen.qap_lp(3, N)
+    a, b = lpgen.qap_matrices(3, N)
+    best = np.inf
+    for perm in itertools.permutations(range(N)):
+        perm = np.array(perm)
+        v = _perm_point(N, perm)
+        assert np.allclose(lp.A1 @ v, lp.b1, atol=1e-12)
+        cost = float(lp.c @ v)
+        assert cost == pytest.approx(float(np.sum(a * b[np.ix_(perm, perm)])), abs=1e-9)
+        best = min(best, cost)
+    r = orc.solve(lp, tol=1e-8, max_iter=400_000)
+    assert r["info"]["status"] == 0
+    ind = K.kkt(lp, r["x"], r["y"], r["z"])
+    assert ind["kkt"] <= 1e-8 * (1 + 1e-6)
+    A1 = sp.csr_matrix((lp.A1.data, lp.A1.indices.astype(np.int32), lp.A1.indptr.astype(np.int32)), shape=lp.A1.shape)
+    res = linprog(lp.c, A_eq=A1, b_eq=lp.b1, bounds=list(zip(lp.l, [None if not np.isfinite(u) else u for u in lp.u])),
+                  method="highs")
+    assert res.status == 0
+    assert abs(ind["pobj"] - res.fun) <= 1e-7 * max(1.0, abs(res.fun))
+    assert res.fun <= best + 1e-9
