@@ -317,6 +317,8 @@ int validate_block(hpr_ctx *ctx, const hpr_csr *B, const char *name, int64_t *ro
     }
     if (B->rows < 0 || B->cols < 0 || B->nnz < 0)
         return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": negative size");
+    if (B->rows >= (int64_t)INT32_MAX || B->cols >= (int64_t)INT32_MAX || B->nnz >= (int64_t)INT32_MAX)
+        return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": sizes beyond 2^31-1 are not supported");
     if (!B->row_ptr || (B->nnz > 0 && (!B->col_idx || !B->val)))
         return fail_arg(ctx, HPR_ERR_ARG, std::string(name) + ": NULL array");
     if (B->row_ptr[0] != 0 || B->row_ptr[B->rows] != B->nnz)

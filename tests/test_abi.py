@@ -129,3 +129,24 @@ def test_invalid_options_rejected(lib, bad):
     with pytest.raises(hpr.HprError) as e:
         hpr.Solver(lp, **bad)
     assert e.value.code == hpr.HPR_ERR_ARG
+
+
+def test_sizes_beyond_32_bit_indices_rejected_before_reading(lib):
+    """A block declaring 2^31 nonzeros is refused from its sizes alone (the 32-bit index
+    layout cannot hold it); the arrays behind it are never read."""
+    import ctypes
+    rp = np.array([0, 1 << 31], dtype=np.int64)
+    ci = np.zeros(1, dtype=np.int32)
+    va = np.ones(1)
+    B = hpr.hpr_csr(1, 4, 1 << 31, rp.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                    ci.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), va.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    out = ctypes.c_void_p()
+    b = np.zeros(1)
+    v4 = np.zeros(4)
+    u4 = np.ones(4)
+    code = lib.hpr_create(ctypes.byref(out), ctypes.byref(B), None, b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          None, v4.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          v4.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          u4.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None)
+    assert code == hpr.HPR_ERR_ARG
+    assert "2^31" in hpr.hpr_last_error(None)
