@@ -480,6 +480,27 @@ EpiNorm epi_norm(hpr_ctx *c, const double *xin, double *out, int q)
     return e;
 }
 
+// residual passes of a check: dual (A^T y_bar) and primal with the M-norm cross term (A x_bar, A dx)
+EpiDual epi_dual(hpr_ctx *ctx)
+{
+    EpiDual d{};
+    d.xa = ctx->ybar; d.xb = ctx->ybar; d.q[0] = Q_RD;
+    d.partials = ctx->partials; d.pstride = ctx->pstride;
+    d.c = ctx->cp; d.zbar = ctx->zbar; d.wc = ctx->wcp;
+    d.ctl = ctx->ctl; d.it = 0;
+    return d;
+}
+
+EpiPrimal epi_primal(hpr_ctx *ctx)
+{
+    EpiPrimal p{};
+    p.xa = ctx->xbar; p.xb = ctx->dx; p.q[0] = Q_RP; p.q[1] = Q_CROSS;
+    p.partials = ctx->partials; p.pstride = ctx->pstride;
+    p.b = ctx->bp; p.wr = ctx->wrp; p.dy = ctx->dy; p.ineq = ctx->ineq;
+    p.ctl = ctx->ctl; p.it = 0;
+    return p;
+}
+
 // one HPR iteration (phase X then phase Y).  store: the phases also store x_bar, z_bar,
 // y_bar, x - x_bar, y - y_bar; check: the two residual passes run and every check
 // quantity is reduced into scal slot `slot`.
@@ -502,16 +523,8 @@ int enqueue_iteration(hpr_ctx *ctx, int it, bool store, bool check, int slot)
         if ((st = launch_sell(ctx, ctx->SA, epi_y<false>(ctx, it)))) return st;
     }
     if (!check) return HPR_OK;
-    EpiDual d{};
-    d.xa = ctx->ybar; d.xb = ctx->ybar; d.q[0] = Q_RD;
-    d.partials = ctx->partials; d.pstride = ctx->pstride;
-    d.c = ctx->cp; d.zbar = ctx->zbar; d.wc = ctx->wcp;
-    if ((st = launch_sell(ctx, ctx->ST, d))) return st;
-    EpiPrimal p{};
-    p.xa = ctx->xbar; p.xb = ctx->dx; p.q[0] = Q_RP; p.q[1] = Q_CROSS;
-    p.partials = ctx->partials; p.pstride = ctx->pstride;
-    p.b = ctx->bp; p.wr = ctx->wrp; p.dy = ctx->dy; p.ineq = ctx->ineq;
-    if ((st = launch_sell(ctx, ctx->SA, p))) return st;
+    if ((st = launch_sell(ctx, ctx->ST, epi_dual(ctx)))) return st;
+    if ((st = launch_sell(ctx, ctx->SA, epi_primal(ctx)))) return st;
     const int nX = ctx->ST.rows ? ctx->ST.grid : 0, nY = ctx->SA.rows ? ctx->SA.grid : 0;
     const int nD = nX, nP = nY;
     return launch_reduce(ctx, {{Q_DX2, nX}, {Q_XX0, nX}, {Q_CX, nX}, {Q_BND, nX},
@@ -1294,7 +1307,7 @@ int solve_begin(hpr_ctx *ctx, double tol)
 
 // control block of the next period: sigma, 1/(lambda sigma) and the Halpern weights of
 // its L iterations; fused_lo / fused_hi: the iterations that fused launches may run
-int period_prepare(hpr_ctx *ctx)
+int period_prepare(hpr_ctx *ctx, bool upload = true)
 {
     SolveState &S = ctx->ss;
     const hpr_options &o = ctx->opt;
@@ -1308,13 +1321,16 @@ int period_prepare(hpr_ctx *ctx)
     h->fused_hi = S.L - 1;
     h->form = ctx->form;
     h->active = S.done ? 0 : 1;
+    h->check_a = S.first_r0 ? 0 : -1;
+    h->check_b = S.L - 1;
     for (int i = 0; i < S.L; ++i) {
         const double tt = (double)(S.t + i);
         h->h[2 * i] = o.halpern ? 1.0 / (tt + 2.0) : 0.0;   // 0 and 1: w = w_target exactly
         h->h[2 * i + 1] = o.halpern ? (tt + 1.0) / (tt + 2.0) : 1.0;
     }
-    CK(cudaMemcpyAsync(ctx->ctl, h, sizeof(DevCtl) + sizeof(double) * 2 * S.L, cudaMemcpyHostToDevice,
-                       ctx->stream));
+    if (upload)
+        CK(cudaMemcpyAsync(ctx->ctl, h, sizeof(DevCtl) + sizeof(double) * 2 * S.L, cudaMemcpyHostToDevice,
+                           ctx->stream));
     return HPR_OK;
 }
 
@@ -1770,14 +1786,27 @@ struct hpr_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<hpr_ctx *> ctxs;
-    MultiUnit *unitsT = nullptr, *unitsA = nullptr;   // fused work lists (A^T and A phases)
-    int nunitsT = 0, nunitsA = 0;
+    MultiTask *tasksT = nullptr, *tasksA = nullptr;   // fused CTA lists (A^T and A phases)
+    int ntasksT = 0, ntasksA = 0;
     SellArgs *sellT64 = nullptr, *sellA64 = nullptr, *sellT32 = nullptr, *sellA32 = nullptr;
     EpiX<false> *ex = nullptr;
     EpiY<false> *ey = nullptr;
     EpiX32<false> *ex32 = nullptr;
     EpiY32<false> *ey32 = nullptr;
+    EpiX<true> *exc = nullptr;
+    EpiY<true> *eyc = nullptr;
+    EpiX32<true> *exc32 = nullptr;
+    EpiY32<true> *eyc32 = nullptr;
+    EpiDual *edual = nullptr;
+    EpiPrimal *eprim = nullptr;
+    RedTask *red = nullptr;
+    int nred = 0;
+    // every context's control block and check scalars in one array each (one copy a period)
+    char *ctl_all = nullptr, *ctl_all_h = nullptr;
+    size_t ctl_stride = 0, ctl_cap_bytes = 0;
+    double *scal_all = nullptr, *scal_all_h = nullptr;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (L, forms present)
+    std::map<std::pair<int, int>, int64_t> graph_nodes;      // kernels in each
     int64_t power_threads = 8;
     double solve_time = 0.0;
     int64_t periods = 0, fused_launches = 0;
@@ -1789,10 +1818,13 @@ void batch_free(hpr_batch *b)
 {
     for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
     b->graphs.clear();
-    void *dev[] = {b->unitsT, b->unitsA, b->sellT64, b->sellA64, b->sellT32, b->sellA32,
-                   b->ex, b->ey, b->ex32, b->ey32};
+    void *dev[] = {b->tasksT, b->tasksA, b->sellT64, b->sellA64, b->sellT32, b->sellA32, b->ex, b->ey,
+                   b->ex32, b->ey32, b->exc, b->eyc, b->exc32, b->eyc32, b->edual, b->eprim, b->red,
+                   b->ctl_all, b->scal_all};
     for (void *p : dev)
         if (p) cudaFree(p);
+    if (b->ctl_all_h) cudaFreeHost(b->ctl_all_h);
+    if (b->scal_all_h) cudaFreeHost(b->scal_all_h);
     for (hpr_ctx *c : b->ctxs) {
         c->stream = c->home_stream;
         c->batched = false;
@@ -1809,24 +1841,30 @@ int upload_table(const std::vector<T> &h, T **d)
     return HPR_OK;
 }
 
-// fused work list of one phase: every context's units, costliest first (ties by context)
-std::vector<MultiUnit> fused_units(const std::vector<hpr_ctx *> &cs, bool transpose)
+// fused CTA list of one phase: every CTA of every context's own launch, costliest first
+// (cost: its 8 work units), ties by context and CTA
+std::vector<MultiTask> fused_tasks(const std::vector<hpr_ctx *> &cs, bool transpose)
 {
-    struct U { float cost; int inst, run; };
-    std::vector<U> all;
+    struct T { float cost; int inst, cta; };
+    std::vector<T> all;
     for (size_t i = 0; i < cs.size(); ++i) {
         const SellDev &M = transpose ? cs[i]->ST : cs[i]->SA;
         if (M.rows == 0) continue;
-        for (int r = 0; r < M.nruns; ++r) all.push_back({M.ucost[(size_t)r], (int)i, r});
+        for (int c = 0; c < M.grid; ++c) {
+            float cost = 0.f;
+            for (int r = c * (TB / 32); r < std::min(M.nruns, (c + 1) * (TB / 32)); ++r) cost += M.ucost[(size_t)r];
+            all.push_back({cost, (int)i, c});
+        }
     }
-    std::stable_sort(all.begin(), all.end(), [](const U &a, const U &b) { return a.cost > b.cost; });
-    std::vector<MultiUnit> out(all.size());
-    for (size_t i = 0; i < all.size(); ++i) out[i] = MultiUnit{all[i].inst, all[i].run};
+    std::stable_sort(all.begin(), all.end(), [](const T &a, const T &b) { return a.cost > b.cost; });
+    std::vector<MultiTask> out(all.size());
+    for (size_t i = 0; i < all.size(); ++i) out[i] = MultiTask{all[i].inst, all[i].cta};
     return out;
 }
 
-// per-context layouts and epilogue operands of the fused launches (allocated once,
-// refreshed before every solve: a solve may reallocate a context's control block)
+// per-context layouts, epilogue operands and reduction tasks of the fused launches
+// (allocated once, refreshed before every solve: a solve may reallocate a context's
+// control block, and a batched solve points it into the batch's array)
 int batch_tables(hpr_batch *b, bool alloc)
 {
     std::vector<SellArgs> sT64, sA64, sT32, sA32;
@@ -1834,7 +1872,15 @@ int batch_tables(hpr_batch *b, bool alloc)
     std::vector<EpiY<false>> ey;
     std::vector<EpiX32<false>> ex32;
     std::vector<EpiY32<false>> ey32;
-    for (hpr_ctx *c : b->ctxs) {
+    std::vector<EpiX<true>> exc;
+    std::vector<EpiY<true>> eyc;
+    std::vector<EpiX32<true>> exc32;
+    std::vector<EpiY32<true>> eyc32;
+    std::vector<EpiDual> ed;
+    std::vector<EpiPrimal> ep;
+    std::vector<RedTask> red;
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        hpr_ctx *c = b->ctxs[i];
         sT64.push_back(sell_of(c->ST, false));
         sA64.push_back(sell_of(c->SA, false));
         sT32.push_back(sell_of(c->ST, true));
@@ -1843,6 +1889,18 @@ int batch_tables(hpr_batch *b, bool alloc)
         ey.push_back(epi_y<false>(c, 0));
         ex32.push_back(epi_x32<false>(c, 0));
         ey32.push_back(epi_y32<false>(c, 0));
+        exc.push_back(epi_x<true>(c, 0));
+        eyc.push_back(epi_y<true>(c, 0));
+        exc32.push_back(epi_x32<true>(c, 0));
+        eyc32.push_back(epi_y32<true>(c, 0));
+        ed.push_back(epi_dual(c));
+        ep.push_back(epi_primal(c));
+        const int nX = c->ST.rows ? c->ST.grid : 0, nY = c->SA.rows ? c->SA.grid : 0;
+        const std::pair<int, int> qs[10] = {{Q_DX2, nX}, {Q_XX0, nX}, {Q_CX, nX}, {Q_BND, nX}, {Q_DY2, nY},
+                                            {Q_YY0, nY}, {Q_BY, nY}, {Q_RD, nX}, {Q_RP, nY}, {Q_CROSS, nY}};
+        for (const auto &q : qs)
+            red.push_back(RedTask{c->partials, c->pstride, q.first, q.second, 0, c->ctl,
+                                  b->scal_all + i * 2 * NQ});
     }
     auto put = [&](auto &h, auto **d) -> int {
         using T = typename std::remove_reference<decltype(h)>::type::value_type;
@@ -1853,38 +1911,47 @@ int batch_tables(hpr_batch *b, bool alloc)
     int st;
     if ((st = put(sT64, &b->sellT64)) || (st = put(sA64, &b->sellA64)) || (st = put(sT32, &b->sellT32)) ||
         (st = put(sA32, &b->sellA32)) || (st = put(ex, &b->ex)) || (st = put(ey, &b->ey)) ||
-        (st = put(ex32, &b->ex32)) || (st = put(ey32, &b->ey32)))
+        (st = put(ex32, &b->ex32)) || (st = put(ey32, &b->ey32)) || (st = put(exc, &b->exc)) ||
+        (st = put(eyc, &b->eyc)) || (st = put(exc32, &b->exc32)) || (st = put(eyc32, &b->eyc32)) ||
+        (st = put(ed, &b->edual)) || (st = put(ep, &b->eprim)) || (st = put(red, &b->red)))
         return st;
+    b->nred = (int)red.size();
     return HPR_OK;
 }
 
-template <class E>
-int launch_multi(hpr_batch *b, const MultiUnit *units, int nunits, const SellArgs *sells, const E *epis, int it)
+template <class E, int MODE, int FORM>
+int launch_multi(hpr_batch *b, const MultiTask *tasks, int ntasks, const SellArgs *sells, const E *epis, int it)
 {
-    if (nunits == 0) return HPR_OK;
-    const int grid = (nunits + TB / 32 - 1) / (TB / 32);
-    k_sell_multi<E><<<grid, TB, 0, b->stream>>>(units, nunits, sells, epis, it);
+    if (ntasks == 0) return HPR_OK;
+    k_sell_multi<E, MODE, FORM><<<ntasks, TB, 0, b->stream>>>(tasks, sells, epis, it);
     if (cudaGetLastError() != cudaSuccess) return HPR_ERR_CUDA;
     b->fused_launches += 1;
     return HPR_OK;
 }
 
-// fused normal iterations 0 .. L-2 of a period (each context takes part in its own range)
+// every context's period of L iterations as fused launches: iterations 0 and L-1 in check
+// mode (with the residual passes and reductions) for the contexts that check there, the
+// others as normal iterations (each context's control block says which it takes part in)
 int enqueue_fused(hpr_batch *b, int L, int forms)
 {
     int st;
-    for (int it = 0; it + 1 < L; ++it) {
-        if (forms & 1) {
-            if ((st = launch_multi(b, b->unitsT, b->nunitsT, b->sellT64, b->ex, it))) return st;
-        }
-        if (forms & 2) {
-            if ((st = launch_multi(b, b->unitsT, b->nunitsT, b->sellT32, b->ex32, it))) return st;
-        }
-        if (forms & 1) {
-            if ((st = launch_multi(b, b->unitsA, b->nunitsA, b->sellA64, b->ey, it))) return st;
-        }
-        if (forms & 2) {
-            if ((st = launch_multi(b, b->unitsA, b->nunitsA, b->sellA32, b->ey32, it))) return st;
+    const int nT = b->ntasksT, nA = b->ntasksA;
+    for (int it = 0; it < L; ++it) {
+        const bool chk = (it == 0 || it == L - 1), nrm = it < L - 1;
+        if (chk && (forms & 1) && (st = launch_multi<EpiX<true>, 1, 0>(b, b->tasksT, nT, b->sellT64, b->exc, it))) return st;
+        if (chk && (forms & 2) && (st = launch_multi<EpiX32<true>, 1, 1>(b, b->tasksT, nT, b->sellT32, b->exc32, it))) return st;
+        if (nrm && (forms & 1) && (st = launch_multi<EpiX<false>, 0, 0>(b, b->tasksT, nT, b->sellT64, b->ex, it))) return st;
+        if (nrm && (forms & 2) && (st = launch_multi<EpiX32<false>, 0, 1>(b, b->tasksT, nT, b->sellT32, b->ex32, it))) return st;
+        if (chk && (forms & 1) && (st = launch_multi<EpiY<true>, 1, 0>(b, b->tasksA, nA, b->sellA64, b->eyc, it))) return st;
+        if (chk && (forms & 2) && (st = launch_multi<EpiY32<true>, 1, 1>(b, b->tasksA, nA, b->sellA32, b->eyc32, it))) return st;
+        if (nrm && (forms & 1) && (st = launch_multi<EpiY<false>, 0, 0>(b, b->tasksA, nA, b->sellA64, b->ey, it))) return st;
+        if (nrm && (forms & 2) && (st = launch_multi<EpiY32<false>, 0, 1>(b, b->tasksA, nA, b->sellA32, b->ey32, it))) return st;
+        if (chk) {
+            if ((st = launch_multi<EpiDual, 1, -1>(b, b->tasksT, nT, b->sellT64, b->edual, it))) return st;
+            if ((st = launch_multi<EpiPrimal, 1, -1>(b, b->tasksA, nA, b->sellA64, b->eprim, it))) return st;
+            k_reduce_multi<<<b->nred, TB, 0, b->stream>>>(b->red, it);
+            if (cudaGetLastError() != cudaSuccess) return HPR_ERR_CUDA;
+            b->fused_launches += 1;
         }
     }
     return HPR_OK;
@@ -1933,13 +2000,16 @@ int hpr_batch_create(hpr_batch **out, int64_t count, hpr_ctx *const *ctxs, void 
     }
     for (hpr_ctx *c : cs) cudaStreamSynchronize(c->stream);
     b->ctxs = cs;
-    std::vector<MultiUnit> uT = fused_units(cs, true), uA = fused_units(cs, false);
+    std::vector<MultiTask> tT = fused_tasks(cs, true), tA = fused_tasks(cs, false);
     int st = HPR_OK;
-    if ((st = upload_table(uT, &b->unitsT)) || (st = upload_table(uA, &b->unitsA)) ||
+    if (cudaMalloc((void **)&b->scal_all, sizeof(double) * 2 * NQ * cs.size()) != cudaSuccess ||
+        cudaMallocHost((void **)&b->scal_all_h, sizeof(double) * 2 * NQ * cs.size()) != cudaSuccess)
+        return fail(HPR_ERR_NOMEM, "hpr_batch_create: check scalars could not be allocated");
+    if ((st = upload_table(tT, &b->tasksT)) || (st = upload_table(tA, &b->tasksA)) ||
         (st = batch_tables(b, true)))
         return fail(st, "hpr_batch_create: device tables could not be allocated or copied");
-    b->nunitsT = (int)uT.size();
-    b->nunitsA = (int)uA.size();
+    b->ntasksT = (int)tT.size();
+    b->ntasksA = (int)tA.size();
     for (hpr_ctx *c : cs) {
         c->stream = b->stream;
         c->batched = true;
@@ -1993,84 +2063,114 @@ int hpr_batch_solve(hpr_batch *b, double tol)
         for (int v : rc)
             if (v != HPR_OK) return v;
     }
+    // every control block in one array for the solve (the contexts' own come back after it)
+    size_t need = 0;
+    for (hpr_ctx *c : cs) need = std::max(need, c->ctl_bytes);
+    const size_t stride = (need + 255) & ~(size_t)255;
+    if (stride > b->ctl_stride) {
+        if (b->ctl_all) cudaFree(b->ctl_all);
+        if (b->ctl_all_h) cudaFreeHost(b->ctl_all_h);
+        b->ctl_all = b->ctl_all_h = nullptr;
+        b->ctl_stride = 0;
+        if (cudaMalloc((void **)&b->ctl_all, stride * cs.size()) != cudaSuccess ||
+            cudaMallocHost((void **)&b->ctl_all_h, stride * cs.size()) != cudaSuccess) {
+            g_static_err = "hpr_batch_solve: control blocks could not be allocated";
+            return HPR_ERR_NOMEM;
+        }
+        b->ctl_stride = stride;
+    }
+    struct Saved { DevCtl *ctl, *ctl_h; size_t bytes; };
+    std::vector<Saved> saved;
+    for (size_t i = 0; i < cs.size(); ++i) {
+        hpr_ctx *c = cs[i];
+        saved.push_back({c->ctl, c->ctl_h, c->ctl_bytes});
+        memset(b->ctl_all_h + i * b->ctl_stride, 0, b->ctl_stride);
+        c->ctl = reinterpret_cast<DevCtl *>(b->ctl_all + i * b->ctl_stride);
+        c->ctl_h = reinterpret_cast<DevCtl *>(b->ctl_all_h + i * b->ctl_stride);
+    }
+    auto restore = [&]() {
+        for (size_t i = 0; i < cs.size(); ++i) {
+            cs[i]->ctl = saved[i].ctl;
+            cs[i]->ctl_h = saved[i].ctl_h;
+            cs[i]->ctl_bytes = saved[i].bytes;
+        }
+    };
     int st = batch_tables(b, false);
     if (st) {
+        restore();
         g_static_err = "hpr_batch_solve: device tables could not be refreshed";
         return st;
     }
     for (hpr_ctx *c : cs) c->ss.ctl_off = false;
+    auto fail = [&](int code, const char *what) {
+        cudaStreamSynchronize(b->stream);
+        restore();
+        if (what) g_static_err = what;
+        return code;
+    };
     for (;;) {
-        std::vector<hpr_ctx *> act;
-        for (hpr_ctx *c : cs)
-            if (!c->ss.done) act.push_back(c);
+        std::vector<size_t> act;
+        for (size_t i = 0; i < cs.size(); ++i)
+            if (!cs[i]->ss.done) act.push_back(i);
         if (act.empty()) break;
         int forms = 0;
         for (hpr_ctx *c : cs) {
             if (c->ss.done) {                // once: its control block takes it out of fused launches
-                if (!c->ss.ctl_off && (st = period_prepare(c))) return st;
+                if (!c->ss.ctl_off && (st = period_prepare(c, false))) return fail(st, nullptr);
                 c->ss.ctl_off = true;
                 continue;
             }
-            if ((st = period_prepare(c))) return st;
+            if ((st = period_prepare(c, false))) return fail(st, nullptr);
             forms |= c->form == 1 ? 2 : 1;
         }
-        const int L = act[0]->ss.L;
-        for (hpr_ctx *c : act)
-            if (c->ss.L != L) {
-                g_static_err = "hpr_batch_solve: contexts out of step";
-                return HPR_ERR_STATE;
+        const int L = cs[act[0]]->ss.L;
+        for (size_t i : act)
+            if (cs[i]->ss.L != L) return fail(HPR_ERR_STATE, "hpr_batch_solve: contexts out of step");
+        if (cudaMemcpyAsync(b->ctl_all, b->ctl_all_h, b->ctl_stride * cs.size(), cudaMemcpyHostToDevice,
+                            b->stream) != cudaSuccess)
+            return fail(HPR_ERR_CUDA, "hpr_batch_solve: control block copy failed");
+        const auto key = std::make_pair(L, forms);
+        auto itg = b->graphs.find(key);
+        if (itg == b->graphs.end()) {
+            if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return fail(HPR_ERR_CUDA, "hpr_batch_solve: graph capture failed");
+            const int64_t before = b->fused_launches;
+            int rr = enqueue_fused(b, L, forms);
+            b->graph_nodes[key] = b->fused_launches - before;
+            b->fused_launches = before;
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+            if (rr || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return fail(rr ? rr : HPR_ERR_CUDA, "hpr_batch_solve: graph capture failed");
             }
-        // iteration 0 in check mode for contexts that start an inner loop
-        if (L > 1)
-            for (hpr_ctx *c : act)
-                if (c->ss.first_r0 && (st = enqueue_iteration(c, 0, true, true, 0))) return st;
-        // fused normal iterations 0 .. L-2
-        if (L > 1) {
-            const auto key = std::make_pair(L, forms);
-            auto itg = b->graphs.find(key);
-            if (itg == b->graphs.end()) {
-                if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HPR_ERR_CUDA;
-                const int64_t before = b->fused_launches;
-                int rr = enqueue_fused(b, L, forms);
-                b->fused_launches = before;
-                cudaGraph_t g = nullptr;
-                cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-                if (rr || e != cudaSuccess) {
-                    if (g) cudaGraphDestroy(g);
-                    g_static_err = "hpr_batch_solve: graph capture failed";
-                    return rr ? rr : HPR_ERR_CUDA;
-                }
-                cudaGraphExec_t ex = nullptr;
-                e = cudaGraphInstantiate(&ex, g, 0);
-                cudaGraphDestroy(g);
-                if (e != cudaSuccess) {
-                    g_static_err = "hpr_batch_solve: graph instantiation failed";
-                    return HPR_ERR_CUDA;
-                }
-                itg = b->graphs.emplace(key, ex).first;
-            }
-            if (cudaGraphLaunch(itg->second, b->stream) != cudaSuccess) return HPR_ERR_CUDA;
-            b->fused_launches += (int64_t)(L - 1) * (((forms & 1) ? 2 : 0) + ((forms & 2) ? 2 : 0));
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(HPR_ERR_CUDA, "hpr_batch_solve: graph instantiation failed");
+            itg = b->graphs.emplace(key, ex).first;
         }
-        // the check iteration, per context
-        for (hpr_ctx *c : act) {
-            if ((st = enqueue_iteration(c, L - 1, true, true, 1))) return st;
-            if ((st = period_readback(c))) return st;
+        if (cudaGraphLaunch(itg->second, b->stream) != cudaSuccess)
+            return fail(HPR_ERR_CUDA, "hpr_batch_solve: graph launch failed");
+        b->fused_launches += b->graph_nodes[key];
+        if (cudaMemcpyAsync(b->scal_all_h, b->scal_all, sizeof(double) * 2 * NQ * cs.size(),
+                            cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+            cudaStreamSynchronize(b->stream) != cudaSuccess)
+            return fail(HPR_ERR_CUDA, "hpr_batch_solve: CUDA error during a period");
+        for (size_t i : act) {
+            hpr_ctx *c = cs[i];
+            memcpy(c->scal_h, b->scal_all_h + i * 2 * NQ, sizeof(double) * 2 * NQ);
+            if ((st = period_after(c, now_s() - c->ss.t0))) return fail(st, nullptr);
         }
-        if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
-            g_static_err = "hpr_batch_solve: CUDA error during a period";
-            return HPR_ERR_CUDA;
-        }
-        for (hpr_ctx *c : act)
-            if ((st = period_after(c, now_s() - c->ss.t0))) return st;
         b->periods++;
     }
     int worst = HPR_OK;
     for (hpr_ctx *c : cs) {
         st = solve_finish(c);
-        if (st < 0) return st;
+        if (st < 0) return fail(st, nullptr);
         if (st != HPR_OK) worst = st;
     }
+    restore();
     b->solve_time = now_s() - t0;
     return worst;
 }

@@ -56,7 +56,9 @@ struct DevCtl {
                               // (batched) launches run for this context
     int form;         // 0: FP64 iterates, 1: FP32 form
     int active;       // 0: the context's solve has ended (fused launches skip it)
-    double pad[4];
+    int check_a, check_b;     // the period's check-mode iterations (-1: none): its first
+                              // (an inner loop starts) and its last
+    double pad[3];
     double h[2];      // h[2i] = 1/(t+2), h[2i+1] = (t+1)/(t+2) for iteration i of the period
 };
 
@@ -324,33 +326,70 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
     }
 }
 
-// Many LPs in one launch (the batched solve): unit u of the fused work list is work unit
-// units[u].run of context units[u].inst, whose layout and epilogue operands come from
-// the per-context tables.  A warp skips its unit unless that context is active, in the
-// form this kernel computes, and iteration `it` of the period is one of its fused ones
-// (its control block says which).  Normal iterations only (no partial sums).
-struct MultiUnit {
-    int inst, run;
+// Many LPs in one launch (the batched solve).  Block b of a fused launch is CTA
+// tasks[b].cta of context tasks[b].inst: its 8 warps take that context's work units
+// 8 cta .. 8 cta + 7, exactly as block `cta` of the context's own launch would, so the
+// per-row arithmetic and the per-CTA partial sums are the same.  The context's layout
+// and epilogue operands come from per-context tables.  A whole block skips unless its
+// context is active, in the form FORM (-1: any), and iteration `it` is one this launch
+// runs for it: MODE 0 (normal iterations) fused_lo <= it < fused_hi, MODE 1 (check-mode
+// iterations and residual passes) it == check_a or it == check_b.
+struct MultiTask {
+    int inst, cta;
 };
 
-template <class E>
-__global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell_multi(const MultiUnit *__restrict__ units,
-                                                                  int nunits, const SellArgs *__restrict__ sells,
+__device__ __forceinline__ bool multi_runs(const DevCtl *c, int mode, int form, int it)
+{
+    if (!c->active || (form >= 0 && c->form != form)) return false;
+    return mode == 0 ? (it >= c->fused_lo && it < c->fused_hi) : (it == c->check_a || it == c->check_b);
+}
+
+template <class E, int MODE, int FORM>
+__global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell_multi(const MultiTask *__restrict__ tasks,
+                                                                  const SellArgs *__restrict__ sells,
                                                                   const E *__restrict__ epis, int it)
 {
-    static_assert(E::NP == 0, "fused launches run normal iterations only");
-    constexpr int FORM = sizeof(typename E::Val) == 4 ? 1 : 0;
-    const int u = blockIdx.x * (TB / 32) + (threadIdx.x >> 5);
-    if (u >= nunits) return;                      // whole warps: no block-wide step follows
-    const MultiUnit mu = units[u];
-    E ee = epis[mu.inst];
-    const DevCtl *c = ee.ctl;
-    if (!c->active || c->form != FORM || it < c->fused_lo || it >= c->fused_hi) return;
+    constexpr int NP = E::NP;
+    static_assert(MODE == 1 || NP == 0, "normal iterations have no partial sums");
+    __shared__ double red[TB / 32];
+    const MultiTask t = tasks[blockIdx.x];
+    E ee = epis[t.inst];
+    if (!multi_runs(ee.ctl, MODE, FORM, it)) return;        // the whole block
     ee.it = it;
     ee.load();
-    const SellArgs S = sells[mu.inst];
-    double part[1] = {0.0};
-    sell_unit(S, ee, mu.run, part);
+    const SellArgs S = sells[t.inst];
+    double part[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int i = 0; i < (NP > 0 ? NP : 1); ++i) part[i] = 0.0;
+    sell_unit(S, ee, t.cta * (TB / 32) + (threadIdx.x >> 5), part);
+    if (NP > 0) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const double s = block_sum(part[i], red);
+            if (threadIdx.x == 0) ee.partials[ee.q[i] * ee.pstride + t.cta] = s;
+        }
+    }
+}
+
+// the check reductions of many contexts: block b sums quantity q of context inst over its
+// cnt CTA partials (the order of k_reduce) into out[slot * NQ + q], slot 1 at the check
+// iteration ending the period, 0 at its first
+struct RedTask {
+    const double *partials;
+    int pstride, q, cnt, pad;
+    const DevCtl *ctl;
+    double *out;
+};
+
+__global__ void __launch_bounds__(TB) k_reduce_multi(const RedTask *__restrict__ tasks, int it)
+{
+    __shared__ double red[TB / 32];
+    const RedTask t = tasks[blockIdx.x];
+    if (!multi_runs(t.ctl, 1, -1, it)) return;
+    double s = 0.0;
+    for (int g = threadIdx.x; g < t.cnt; g += TB) s += t.partials[t.q * t.pstride + g];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) t.out[(it == t.ctl->check_b ? NQ : 0) + t.q] = s;
 }
 
 // ------------------------------------------------------------------ epilogues
@@ -561,6 +600,8 @@ struct EpiDual {
     double *partials;
     int pstride;
     const double *c, *zbar, *wc;
+    const DevCtl *ctl;           // batched launches only: whether this pass runs
+    int it;
     struct Pre { double c, z, w; };
     __device__ __forceinline__ void load() {}
     __device__ __forceinline__ Pre prefetch(int j) const { return Pre{c[j], zbar[j], wc[j]}; }
@@ -582,6 +623,8 @@ struct EpiPrimal {
     int pstride;
     const double *b, *wr, *dy;
     const unsigned char *ineq;
+    const DevCtl *ctl;           // batched launches only: whether this pass runs
+    int it;
     struct Pre { double b, w, dy; unsigned char ineq; };
     __device__ __forceinline__ void load() {}
     __device__ __forceinline__ Pre prefetch(int i) const { return Pre{b[i], wr[i], dy[i], ineq[i]}; }
