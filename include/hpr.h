@@ -114,6 +114,11 @@ typedef struct {
                                  residual rise above its value at the decision: the next
                                  restart then keeps Algorithm 3's value (a fallback) */
     uint64_t policy_seed;
+    int64_t persistent;       /* the persistent single-CTA path: one CTA of 1024 threads runs the
+                                 power method and all of Algorithm 2 on the device, iterates in
+                                 shared memory (LPs with 56 n + 48 m bytes <= 200 KB).  0 never;
+                                 1 (default) when the LP fits and the solve is plain FP64 without
+                                 tracing, time limit or policy; 2 always (HPR_ERR_ARG if it cannot) */
 } hpr_options;
 
 /* Result summary (original, unscaled problem). */

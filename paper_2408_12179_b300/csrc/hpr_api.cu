@@ -17,6 +17,7 @@
 #include "hpr.h"
 #include "hpr_device.cuh"
 #include "hpr_mlp.cuh"
+#include "hpr_small.cuh"
 
 #include <cuda_runtime.h>
 
@@ -151,6 +152,9 @@ struct hpr_ctx {
     SolveState ss;
     __nv_bfloat16 *policy_wb = nullptr;   // sigma policy network (BF16), its input and output
     float *policy_w32 = nullptr, *policy_x = nullptr, *policy_q = nullptr;
+    hpr_check_record *small_recs = nullptr;   // persistent path: its check records and results
+    double *small_out = nullptr;
+    int small_cap = 0;
     bool batched = false;         // owned by a batch: solved only through hpr_batch_solve
     std::vector<hpr_check_record> checks;
     std::string err;
@@ -357,7 +361,7 @@ void free_all(hpr_ctx *c)
                    c->l_s, c->u_s, c->l_o, c->u_o, c->x, c->x0, c->xhat, c->xbar,
                    c->zbar, c->dx, c->y, c->y0, c->ybar, c->dy, c->xo, c->yo, c->zo,
                    c->partials, c->scal, c->ctl, c->pctl, c->trace, c->policy_wb, c->policy_w32,
-                   c->policy_x, c->policy_q};
+                   c->policy_x, c->policy_q, c->small_recs, c->small_out};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->scal_h) cudaFreeHost(c->scal_h);
@@ -1032,6 +1036,7 @@ int hpr_default_options(hpr_options *o)
     o->unit_cost_a = o->unit_cost_t = 0.0;
     o->sigma_policy = 0;
     o->policy_seed = 0x5167;
+    o->persistent = 1;
     return HPR_OK;
 }
 
@@ -1052,6 +1057,7 @@ static int check_options(hpr_ctx *ctx, const hpr_options *o)
     if (o->reflect != 0 && o->reflect != 1) return fail_arg(ctx, HPR_ERR_ARG, "reflect must be 0 or 1");
     if (o->autotune != 0 && o->autotune != 1) return fail_arg(ctx, HPR_ERR_ARG, "autotune must be 0 or 1");
     if (o->sigma_policy < 0 || o->sigma_policy > 2) return fail_arg(ctx, HPR_ERR_ARG, "sigma_policy must be 0, 1 or 2");
+    if (o->persistent < 0 || o->persistent > 2) return fail_arg(ctx, HPR_ERR_ARG, "persistent must be 0, 1 or 2");
     if (o->sell_steps_a < 0 || o->sell_steps_a > 4096 || o->sell_steps_t < 0 || o->sell_steps_t > 4096)
         return fail_arg(ctx, HPR_ERR_ARG, "sell_steps must be in [0, 4096]");
     if (!(o->unit_cost_a >= 0.0) || !(o->unit_cost_t >= 0.0) || o->unit_cost_a > 1e9 || o->unit_cost_t > 1e9)
@@ -1581,6 +1587,109 @@ int solve_finish(hpr_ctx *ctx)
     return S.status;
 }
 
+constexpr size_t SMALL_SMEM_MAX = 200 * 1024;
+
+// whether the persistent single-CTA path can run this solve (and why not)
+const char *small_unfit(const hpr_ctx *ctx)
+{
+    const hpr_options &o = ctx->opt;
+    if (hprsmall::small_smem_bytes((int)ctx->m, (int)ctx->n, ctx->nnz, false) > SMALL_SMEM_MAX)
+        return "the iterates do not fit in shared memory";
+    if (o.precision != 0) return "the FP32 form";
+    if (o.trace_iters > 0) return "tracing";
+    if (o.time_limit_s > 0.0) return "a time limit";
+    if (o.sigma_policy != 0) return "a sigma policy";
+    return nullptr;
+}
+
+int solve_small(hpr_ctx *ctx, double tol)
+{
+    using namespace hprsmall;
+    const hpr_options &o = ctx->opt;
+    const int64_t n = ctx->n, m = ctx->m;
+    cudaStream_t s = ctx->stream;
+    ctx->solved = false;
+    ctx->checks.clear();
+    ctx->trace_written = 0;
+    CK(cudaStreamSynchronize(s));
+    SolveState &S = ctx->ss;
+    S = SolveState{};
+    S.tol = tol;
+    S.t0 = now_s();
+    ctx->launches = 0;
+    const int cap = (int)std::min<int64_t>(1 << 16, 2 * (o.max_iter / o.check_every) + 16);
+    if (cap > ctx->small_cap) {                // kept between solves
+        if (ctx->small_recs) cudaFree(ctx->small_recs);
+        ctx->small_recs = nullptr;
+        ctx->small_cap = 0;
+        DALLOC(ctx->small_recs, cap);
+        ctx->small_cap = cap;
+    }
+    if (!ctx->small_out) DALLOC(ctx->small_out, SO_LEN);
+    hpr_check_record *recs = ctx->small_recs;
+    double *out = ctx->small_out;
+    SmallArgs A{};
+    A.m = (int)m; A.m1 = (int)ctx->m1; A.n = (int)n;
+    A.rp = ctx->A_rp; A.ci = ctx->A_ci; A.val = ctx->A_val;
+    A.trp = ctx->T_rp; A.tci = ctx->T_ci; A.tval = ctx->T_val;
+    A.b = ctx->b_s; A.c = ctx->c_s; A.l = ctx->l_s; A.u = ctx->u_s; A.wr = ctx->wr; A.wc = ctx->wc;
+    A.beta_b = ctx->beta_b; A.beta_c = ctx->beta_c; A.norm_b = ctx->norm_b; A.norm_c = ctx->norm_c;
+    A.tol = tol; A.alpha1 = o.alpha1; A.alpha2 = o.alpha2; A.alpha3 = o.alpha3; A.sigma0 = o.sigma0;
+    A.lambda_fixed = o.lambda_fixed; A.power_tol = o.power_tol;
+    A.max_iter = o.max_iter; A.check_every = o.check_every; A.power_max_iter = std::max<int64_t>(1, o.power_max_iter);
+    A.seed = o.seed;
+    A.restart = (int)o.restart; A.sigma_update = (int)o.sigma_update; A.halpern = (int)o.halpern;
+    A.reflect = (int)o.reflect;
+    // lanes per row: the largest power of two (<= 32, <= the mean row length) that still gives
+    // every row its lanes in one pass
+    auto lanes = [&](int64_t rows) {
+        const double mean = (double)ctx->nnz / (double)std::max<int64_t>(rows, 1);
+        int L = 1;
+        while (L < 32 && (int64_t)(2 * L) * rows <= NT && 2 * L <= mean) L *= 2;
+        return L;
+    };
+    A.LA = lanes(m);
+    A.LT = lanes(n);
+    A.nnz = (int)ctx->nnz;
+    A.mat_smem = small_smem_bytes((int)m, (int)n, ctx->nnz, true) <= SMALL_SMEM_MAX ? 1 : 0;
+    A.perm_r = ctx->perm_r; A.perm_c = ctx->perm_c;
+    A.xbar_out = ctx->xbar; A.ybar_out = ctx->ybar; A.zbar_out = ctx->zbar;
+    A.recs = recs; A.rec_cap = cap; A.out = out;
+    const size_t smem = small_smem_bytes((int)m, (int)n, ctx->nnz, A.mat_smem != 0);
+    int st = HPR_OK;
+    cudaError_t e = cudaFuncSetAttribute(k_solve_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        k_solve_small<<<1, NT, smem, s>>>(A);
+        e = cudaGetLastError();
+    }
+    double h[SO_LEN];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail_cuda(ctx, e, "solve_small", __LINE__);
+    if (st == HPR_OK) {
+        ctx->launches = 1;
+        const int64_t nrec = std::min<int64_t>((int64_t)h[SO_NREC], cap);
+        ctx->checks.resize((size_t)nrec);
+        if (nrec && cudaMemcpy(ctx->checks.data(), recs, sizeof(hpr_check_record) * nrec, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = fail_arg(ctx, HPR_ERR_CUDA, "solve_small: check records");
+        ctx->lambda = h[SO_LAMBDA];
+        ctx->power_iters = (int64_t)h[SO_POWER_ITERS];
+        ctx->power_time = h[SO_POWER_S];
+        S.lambda = h[SO_LAMBDA];
+        S.k = (int64_t)h[SO_ITERS]; S.r = (int64_t)h[SO_RESTARTS]; S.sigma = h[SO_SIGMA];
+        S.status = (int)h[SO_STATUS];
+        S.last_pobj = h[SO_POBJ]; S.last_dobj = h[SO_DOBJ]; S.last_ep = h[SO_ERRP]; S.last_ed = h[SO_ERRD];
+        S.last_gap = h[SO_GAP]; S.last_kkt = h[SO_KKT];
+        S.time_1e4 = h[SO_T1E4] >= 0.0 ? h[SO_T1E4] : -1.0;
+        S.iters_1e4 = (int64_t)h[SO_I1E4];
+        S.done = true;
+        if (S.status == HPR_ERR_NUMERIC)
+            st = fail_arg(ctx, HPR_ERR_NUMERIC, "non-finite residual at iteration " + std::to_string(S.k - 1));
+    }
+    if (st) return st;
+    return solve_finish(ctx);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1591,6 +1700,12 @@ int hpr_solve(hpr_ctx *ctx, double tol)
     if (!(tol > 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "tol must be > 0");
     if (ctx->batched) return fail_arg(ctx, HPR_ERR_STATE, "the context belongs to a batch");
     cudaSetDevice(ctx->device);
+    if (ctx->opt.persistent) {
+        const char *why = small_unfit(ctx);
+        if (!why) return solve_small(ctx, tol);
+        if (ctx->opt.persistent == 2)
+            return fail_arg(ctx, HPR_ERR_ARG, std::string("persistent = 2 but the single-CTA path cannot run: ") + why);
+    }
     int st = solve_begin(ctx, tol);
     if (st) return st;
     SolveState &S = ctx->ss;

@@ -83,7 +83,7 @@ def evaluate(lps, w, tol=1e-8, max_iter=2_000_000):
     """Per LP: iterations and seconds with Algorithm 3 and with the learned policy."""
     rows = []
     for lp in lps:
-        with hpr.Solver(lp, max_iter=max_iter) as s:
+        with hpr.Solver(lp, max_iter=max_iter, persistent=0) as s:   # both runs on the same path
             base = s.solve(tol)["info"]
             s.set_policy(w)
             s.set_options(sigma_policy=2)

@@ -35,7 +35,7 @@ CAP = 20_000
 
 
 def _solo(lp, **opts):
-    with hpr.Solver(lp, **opts) as s:
+    with hpr.Solver(lp, persistent=0, **opts) as s:     # the multi-CTA path, as in a batch
         return s.solve(1e-8)
 
 
