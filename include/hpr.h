@@ -114,6 +114,9 @@ typedef struct {
                                  residual rise above its value at the decision: the next
                                  restart then keeps Algorithm 3's value (a fallback) */
     uint64_t policy_seed;
+    double policy_margin;     /* sigma_policy 2: a multiplier other than 1 (a = 2) is taken only
+                                 when its predicted outcome beats a = 2's by more than this
+                                 (log10 KKT units; default 0) */
     int64_t persistent;       /* the persistent single-CTA path: one CTA of 1024 threads runs the
                                  power method and all of Algorithm 2 on the device, iterates in
                                  shared memory (LPs with 56 n + 48 m bytes <= 200 KB).  0 never;

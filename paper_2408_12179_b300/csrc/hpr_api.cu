@@ -1036,6 +1036,7 @@ int hpr_default_options(hpr_options *o)
     o->unit_cost_a = o->unit_cost_t = 0.0;
     o->sigma_policy = 0;
     o->policy_seed = 0x5167;
+    o->policy_margin = 0.0;
     o->persistent = 1;
     return HPR_OK;
 }
@@ -1058,6 +1059,8 @@ static int check_options(hpr_ctx *ctx, const hpr_options *o)
     if (o->autotune != 0 && o->autotune != 1) return fail_arg(ctx, HPR_ERR_ARG, "autotune must be 0 or 1");
     if (o->sigma_policy < 0 || o->sigma_policy > 2) return fail_arg(ctx, HPR_ERR_ARG, "sigma_policy must be 0, 1 or 2");
     if (o->persistent < 0 || o->persistent > 2) return fail_arg(ctx, HPR_ERR_ARG, "persistent must be 0, 1 or 2");
+    if (!(o->policy_margin >= 0.0) || o->policy_margin > 100.0)
+        return fail_arg(ctx, HPR_ERR_ARG, "policy_margin must be in [0, 100]");
     if (o->sell_steps_a < 0 || o->sell_steps_a > 4096 || o->sell_steps_t < 0 || o->sell_steps_t > 4096)
         return fail_arg(ctx, HPR_ERR_ARG, "sell_steps must be in [0, 4096]");
     if (!(o->unit_cost_a >= 0.0) || !(o->unit_cost_t >= 0.0) || o->unit_cost_a > 1e9 || o->unit_cost_t > 1e9)
@@ -1249,6 +1252,7 @@ int policy_choose(hpr_ctx *ctx, int *action)
     int best = 0;
     for (int a = 1; a < hprmlp::OUT; ++a)
         if (q[a] < q[best]) best = a;
+    if (!(q[best] < q[2] - ctx->opt.policy_margin)) best = 2;   // not clearly better: Algorithm 3's
     *action = best;
     return HPR_OK;
 }

@@ -12,9 +12,12 @@ Data: solves with ``sigma_policy = 1`` draw the multiplier at random (SplitMix64
 outcome = log10 KKT at the `horizon`-th periodic check after the decision (or at the end
 of the solve) minus log10 KKT at the decision: lower is better.
 
-``python -m paper_2408_12179_b300.policy [n_train n_eval weights.npy]`` trains on seeded
-small instances of the medium planted and multicommodity-flow families and evaluates on
-held-out ones (one GPU), printing one JSON line.
+``python -m paper_2408_12179_b300.policy eval weights.npy n_eval n_large margin...`` only
+evaluates given weights, once per margin (``policy_margin``).
+``python -m paper_2408_12179_b300.policy [n_train n_eval weights.npy n_large]`` trains on
+seeded small instances of the medium planted and multicommodity-flow families and
+evaluates on held-out ones of the same sizes and on `n_large` held-out medium planted LPs
+at scale 0.05 (25k columns) (one GPU), printing one JSON line.
 """
 from __future__ import annotations
 
@@ -79,14 +82,14 @@ def train(X, A, Y, epochs=200, batch=128, lr=1e-3, seed=1):
     return hpr.mlp_train(init_weights(seed), X, A, Y, epochs=epochs, batch=batch, lr=lr, seed=seed)
 
 
-def evaluate(lps, w, tol=1e-8, max_iter=2_000_000):
+def evaluate(lps, w, tol=1e-8, max_iter=2_000_000, margin=0.0):
     """Per LP: iterations and seconds with Algorithm 3 and with the learned policy."""
     rows = []
     for lp in lps:
         with hpr.Solver(lp, max_iter=max_iter, persistent=0) as s:   # both runs on the same path
             base = s.solve(tol)["info"]
             s.set_policy(w)
-            s.set_options(sigma_policy=2)
+            s.set_options(sigma_policy=2, policy_margin=float(margin))
             pol = s.solve(tol)["info"]
         rows.append(dict(name=lp.name, rule_iters=int(base["iters"]), rule_s=base["solve_time_s"],
                          rule_status=int(base["status"]), policy_iters=int(pol["iters"]),
@@ -107,9 +110,35 @@ def training_family(count, seed0=0):
     return out
 
 
+def summary(rows):
+    ok = [r for r in rows if r["rule_status"] == 0 and r["policy_status"] == 0]
+    gm = math.exp(sum(math.log(r["policy_iters"] / r["rule_iters"]) for r in ok) / max(len(ok), 1))
+    dec = sum(r["decisions"] for r in rows)
+    fb = sum(r["fallbacks"] for r in rows)
+    return dict(n=len(rows), converged_both=len(ok), iters_ratio_geomean=gm,
+                time_rule_s=sum(r["rule_s"] for r in rows), time_policy_s=sum(r["policy_s"] for r in rows),
+                worse=sum(r["policy_iters"] > r["rule_iters"] for r in ok), decisions=dec, fallbacks=fb,
+                fallback_rate=fb / max(dec + fb, 1))
+
+
+def main_eval(argv):
+    """eval weights.npy n_eval n_large margin [margin ...]: held-out evaluation only."""
+    hpr.load()
+    w = np.load(argv[2])
+    n_eval, n_large = int(argv[3]), int(argv[4])
+    small = training_family(n_eval, 10_000)
+    large = [lpgen.planted_medium(20_000 + i, 0.05) for i in range(n_large)]
+    for mg in argv[5:]:
+        rs, rl = evaluate(small, w, margin=float(mg)), evaluate(large, w, margin=float(mg))
+        print(json.dumps(dict(margin=float(mg), small=summary(rs), large=summary(rl) if rl else None)), flush=True)
+
+
 def main(argv):
+    if len(argv) > 1 and argv[1] == "eval":
+        return main_eval(argv)
     n_train = int(argv[1]) if len(argv) > 1 else 40
     n_eval = int(argv[2]) if len(argv) > 2 else 10
+    n_large = int(argv[4]) if len(argv) > 4 else 0
     hpr.load()
     t0 = time.time()
     X, A, Y = collect(training_family(n_train, 0), seeds=(11, 12))
@@ -118,15 +147,12 @@ def main(argv):
     t2 = time.time()
     held = training_family(n_eval, 10_000)
     rows = evaluate(held, w)
+    large = evaluate([lpgen.planted_medium(20_000 + i, 0.05) for i in range(n_large)], w) if n_large else []
     t3 = time.time()
-    ok = [r for r in rows if r["rule_status"] == 0 and r["policy_status"] == 0]
-    gm = math.exp(sum(math.log(r["policy_iters"] / r["rule_iters"]) for r in ok) / max(len(ok), 1))
-    dec = sum(r["decisions"] for r in rows)
-    fb = sum(r["fallbacks"] for r in rows)
     print(json.dumps(dict(samples=int(len(Y)), collect_s=t1 - t0, train_s=t2 - t1, eval_s=t3 - t2,
                           loss_first=float(hist[0]), loss_last=float(hist[-1]),
-                          iters_ratio_geomean=gm, decisions=dec, fallbacks=fb,
-                          fallback_rate=fb / max(dec + fb, 1), rows=rows)))
+                          small=summary(rows), large=summary(large) if large else None,
+                          rows=rows, large_rows=large)))
     if len(argv) > 3:                       # where to keep the trained weights
         np.save(argv[3], w)
 
