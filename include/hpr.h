@@ -122,6 +122,9 @@ typedef struct {
                                  shared memory (LPs with 56 n + 48 m bytes <= 200 KB).  0 never;
                                  1 (default) when the LP fits and the solve is plain FP64 without
                                  tracing, time limit or policy; 2 always (HPR_ERR_ARG if it cannot) */
+    int64_t pdl;              /* 1 (default): the two phases of a normal iteration are launched as
+                                 programmatic dependents of the kernel before them, so that their
+                                 set-up overlaps its tail; 0: plain stream order */
 } hpr_options;
 
 /* Result summary (original, unscaled problem). */

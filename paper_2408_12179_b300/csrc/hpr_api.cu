@@ -404,6 +404,7 @@ SellArgs sell_of(const SellDev &d, bool fp32, const int *skip = nullptr)
     a.rows = d.rows; a.nslices = d.nslices; a.srow = d.srow; a.sptr = d.sptr; a.slg = d.slg;
     a.wstart = d.wstart; a.nruns = d.nruns; a.col = d.col; a.skip = skip;
     a.val = fp32 ? (const void *)d.val32 : (const void *)d.val;
+    a.trigger_from = INT32_MAX;
     return a;
 }
 
@@ -423,6 +424,30 @@ int launch_sell(hpr_ctx *ctx, const SellDev &M, const E &e, const int *skip = nu
     if (M.rows == 0) return HPR_OK;
     k_sell<E><<<M.grid, TB, 0, ctx->stream>>>(sell_of(M, sizeof(typename E::Val) == 4, skip), e);
     CKL();
+    ctx->launches += 1;
+    return HPR_OK;
+}
+
+// a normal-iteration phase launched as a programmatic dependent of the kernel before it:
+// the CTAs of its last wave (the ones resident at once) let the next phase launch early
+template <class E>
+int launch_sell_pdl(hpr_ctx *ctx, const SellDev &M, const E &e)
+{
+    if (M.rows == 0) return HPR_OK;
+    if (!ctx->opt.pdl) return launch_sell(ctx, M, e);
+    SellArgs a = sell_of(M, sizeof(typename E::Val) == 4);
+    a.trigger_from = std::max(0, M.grid - SELL_CTAS_PER_SM * ctx->num_sms);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)M.grid);
+    cfg.blockDim = dim3(TB);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_sell<E>, a, e));
     ctx->launches += 1;
     return HPR_OK;
 }
@@ -516,15 +541,15 @@ int enqueue_iteration(hpr_ctx *ctx, int it, bool store, bool check, int slot)
             if ((st = launch_sell(ctx, ctx->ST, epi_x32<true>(ctx, it)))) return st;
             if ((st = launch_sell(ctx, ctx->SA, epi_y32<true>(ctx, it)))) return st;
         } else {
-            if ((st = launch_sell(ctx, ctx->ST, epi_x32<false>(ctx, it)))) return st;
-            if ((st = launch_sell(ctx, ctx->SA, epi_y32<false>(ctx, it)))) return st;
+            if ((st = launch_sell_pdl(ctx, ctx->ST, epi_x32<false>(ctx, it)))) return st;
+            if ((st = launch_sell_pdl(ctx, ctx->SA, epi_y32<false>(ctx, it)))) return st;
         }
     } else if (store || check) {
         if ((st = launch_sell(ctx, ctx->ST, epi_x<true>(ctx, it)))) return st;
         if ((st = launch_sell(ctx, ctx->SA, epi_y<true>(ctx, it)))) return st;
     } else {
-        if ((st = launch_sell(ctx, ctx->ST, epi_x<false>(ctx, it)))) return st;
-        if ((st = launch_sell(ctx, ctx->SA, epi_y<false>(ctx, it)))) return st;
+        if ((st = launch_sell_pdl(ctx, ctx->ST, epi_x<false>(ctx, it)))) return st;
+        if ((st = launch_sell_pdl(ctx, ctx->SA, epi_y<false>(ctx, it)))) return st;
     }
     if (!check) return HPR_OK;
     if ((st = launch_sell(ctx, ctx->ST, epi_dual(ctx)))) return st;
@@ -1038,6 +1063,7 @@ int hpr_default_options(hpr_options *o)
     o->policy_seed = 0x5167;
     o->policy_margin = 0.0;
     o->persistent = 1;
+    o->pdl = 1;
     return HPR_OK;
 }
 
@@ -1059,6 +1085,7 @@ static int check_options(hpr_ctx *ctx, const hpr_options *o)
     if (o->autotune != 0 && o->autotune != 1) return fail_arg(ctx, HPR_ERR_ARG, "autotune must be 0 or 1");
     if (o->sigma_policy < 0 || o->sigma_policy > 2) return fail_arg(ctx, HPR_ERR_ARG, "sigma_policy must be 0, 1 or 2");
     if (o->persistent < 0 || o->persistent > 2) return fail_arg(ctx, HPR_ERR_ARG, "persistent must be 0, 1 or 2");
+    if (o->pdl != 0 && o->pdl != 1) return fail_arg(ctx, HPR_ERR_ARG, "pdl must be 0 or 1");
     if (!(o->policy_margin >= 0.0) || o->policy_margin > 100.0)
         return fail_arg(ctx, HPR_ERR_ARG, "policy_margin must be in [0, 100]");
     if (o->sell_steps_a < 0 || o->sell_steps_a > 4096 || o->sell_steps_t < 0 || o->sell_steps_t > 4096)

@@ -189,7 +189,19 @@ struct SellArgs {
     const void *val;      // stored values, double or float (E::Val); padding: 0
     const int *col;       // stored column indices (padding: 0)
     const int *skip;      // optional: the kernel does nothing while *skip != 0
+    int trigger_from;     // programmatic launch: CTAs from this index on let the next kernel
+                          // start once they have waited for the previous one (others: at exit)
 };
+
+// Programmatic dependent launch (the phases of a normal iteration are launched with it):
+// the work before griddepcontrol.wait -- unit metadata and the epilogue operands, none of
+// them written by the kernel just before -- overlaps that kernel's tail; both instructions
+// are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void dep_wait_and_trigger(const SellArgs &S)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if ((int)blockIdx.x >= S.trigger_from) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // E supplies the value type Val (double or float) of the stored values and gathered
 // vectors, NV gathered vectors xa (, xb), NP partial sums (ids q[]), a Pre record of
@@ -200,6 +212,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
     constexpr int NV = E::NV;
     using V = typename E::Val;
     const int lane = threadIdx.x & 31;
+    bool waited = false;
     int buf_r0 = 0, buf_n = 0;                   // rows [buf_r0, buf_r0 + buf_n) hold sums
     double buf0 = 0.0, buf1 = 0.0;               // lane t: sum of row buf_r0 + t
     typename E::Pre pre{};
@@ -219,6 +232,10 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
         if (buf_n == 0) {
             buf_r0 = r0;                          // operands of the next 32 rows, early
             pre = ee.prefetch(min(r0 + lane, S.rows - 1));
+            if (!waited) {                        // the gathered vector is the previous kernel's output
+                dep_wait_and_trigger(S);
+                waited = true;
+            }
         }
         const V *pv = static_cast<const V *>(S.val) + base + lane;
         const int *pc = S.col + base + lane;
@@ -302,6 +319,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
             buf_n = 0;
         }
     }
+    if (!waited) dep_wait_and_trigger(S);        // warps without a work unit take part too
 }
 
 template <class E>

@@ -49,7 +49,7 @@ class hpr_options(ctypes.Structure):
                 ("sell_steps_t", ctypes.c_int64), ("unit_cost_a", ctypes.c_double),
                 ("unit_cost_t", ctypes.c_double), ("sigma_policy", ctypes.c_int64),
                 ("policy_seed", ctypes.c_uint64), ("policy_margin", ctypes.c_double),
-                ("persistent", ctypes.c_int64)]
+                ("persistent", ctypes.c_int64), ("pdl", ctypes.c_int64)]
 
 
 class hpr_info(ctypes.Structure):

@@ -268,3 +268,18 @@ def test_state_errors():
         assert e.value.code == hpr.HPR_ERR_STATE
         with pytest.raises(hpr.HprError):
             s.trace(0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_programmatic_launch_changes_nothing(precision):
+    """Launching the normal-iteration phases as programmatic dependents (their set-up
+    overlapping the previous kernel's tail) leaves every result bit-identical."""
+    lp = lpgen.planted_medium(4, 0.01)
+    out = []
+    for pdl in (0, 1):
+        with hpr.Solver(lp, persistent=0, pdl=pdl, precision=precision, max_iter=20_000) as s:
+            out.append(s.solve(1e-8))
+    a, b = out
+    assert a["info"]["iters"] == b["info"]["iters"] and a["info"]["restarts"] == b["info"]["restarts"]
+    for key in ("x", "y", "z"):
+        assert np.array_equal(a[key], b[key]), key
