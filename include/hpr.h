@@ -240,9 +240,10 @@ int hpr_power_noalloc(int64_t m, int64_t n, const int32_t *A_row_ptr, const int3
                       const double *At_val, uint64_t seed, int64_t max_iter, double tol,
                       double *u, double *s, void *cuda_stream, double *lambda, int64_t *iters);
 
-/* Layout of the context's sliced-ELL copies (after autotuning, if asked): for A (index 0)
- * and A^T (index 1) the lanes-per-row bound, the work-unit size and the number of work
- * units; any pointer may be NULL. */
+/* Layout of the context's sliced-ELL copies (no counterpart in the paper: a storage choice
+ * of this library), after autotuning if asked: for A (index 0) and A^T (index 1) the
+ * lanes-per-row bound, the work-unit size and the number of work units; any pointer may
+ * be NULL.  Returns HPR_OK or HPR_ERR_ARG (ctx NULL). */
 int hpr_get_layout(const hpr_ctx *ctx, int64_t *sell_steps, double *unit_cost, int64_t *units);
 
 /* ---- Batched solve (no counterpart in the paper: many independent LPs in lock step).
@@ -283,10 +284,12 @@ void hpr_batch_destroy(hpr_batch *batch);
  * [0, 5), non-finite input) or HPR_ERR_NOMEM / HPR_ERR_CUDA, detail in hpr_last_error(NULL). */
 int hpr_mlp_param_count(void);
 /* The policy a context uses with sigma_policy = 2: w (hpr_mlp_param_count() FP32 values,
- * host) is copied; NULL removes it (sigma_policy 2 then behaves as 0). */
+ * host) is copied; NULL removes it (sigma_policy 2 then behaves as 0).  Returns HPR_OK,
+ * HPR_ERR_ARG (ctx NULL or a non-finite weight), HPR_ERR_NOMEM or HPR_ERR_CUDA. */
 int hpr_set_policy(hpr_ctx *ctx, const float *w);
 /* The 64 features of check record `rec` of the last solve (as the policy sees them at a
- * restart decided at that check) into out (host, 64 floats). */
+ * restart decided at that check) into out (host, 64 floats).  HPR_ERR_ARG when rec is not
+ * a record of the last solve. */
 int hpr_policy_features(const hpr_ctx *ctx, int64_t rec, float *out);
 /* Q (n x 5): the outputs for each row of X. */
 int hpr_mlp_infer(const float *w, int64_t n, const float *X, float *Q);
