@@ -592,3 +592,34 @@ def test_qap_lp_relaxes_the_qap(orc, N):
     assert res.status == 0
     assert abs(ind["pobj"] - res.fun) <= 1e-7 * max(1.0, abs(res.fun))
     assert res.fun <= best + 1e-9
+
+
+# ------------------------------------------------------------------ degenerate LPs
+
+def test_fixed_variables_keep_the_planted_optimum(orc):
+    """Fixing columns at their planted values (l = u = x*_j) keeps x* optimal (both bounds
+    active, z*_j of either sign is allowed): the oracle reaches the planted objective."""
+    lp = lpgen.planted_tiny(3)
+    fix = np.arange(0, lp.n, 7)
+    lp.l = lp.l.copy(); lp.u = lp.u.copy()
+    lp.l[fix] = lp.x_star[fix]
+    lp.u[fix] = lp.x_star[fix]
+    r = orc.solve(lp, tol=1e-8, max_iter=400_000)
+    assert r["info"]["status"] == 0
+    assert np.array_equal(r["x"][fix], lp.x_star[fix])
+    ind = K.kkt(lp, r["x"], r["y"], r["z"])
+    assert ind["kkt"] <= 1e-8 * (1 + 1e-6)
+    assert abs(ind["pobj"] - lp.planted_objective) <= 1e-7 * abs(lp.planted_objective)
+
+
+def test_infeasible_lp_runs_to_the_cap(orc):
+    """An infeasible LP (x1 + x2 = 1 and x1 + x2 >= 3): the iteration stays finite, stops at
+    max_iter, and its primal residual does not vanish."""
+    A1 = lpgen._canonical(sp.csr_matrix(np.array([[1.0, 1.0]])))
+    A2 = lpgen._canonical(sp.csr_matrix(np.array([[1.0, 1.0]])))
+    lp = lpgen.LP(A1, A2, np.array([1.0]), np.array([3.0]), np.array([1.0, 2.0]), np.zeros(2), np.full(2, 10.0))
+    r = orc.solve(lp, tol=1e-8, max_iter=3000)
+    assert r["info"]["status"] == 1
+    assert np.all(np.isfinite(r["x"])) and np.all(np.isfinite(r["y"]))
+    assert r["info"]["err_p"] > 1e-3
+    assert K.kkt(lp, r["x"], r["y"], r["z"])["err_p"] > 1e-3
