@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "hpr_api.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", "hpr_device.cuh"), os.path.join(HERE, "csrc", "hpr_mlp.cuh"),
+              os.path.join(HERE, "csrc", "hpr_small.cuh"),
               os.path.join(ROOT, "include", "hpr.h")]
 LIB = os.path.join(HERE, "libhpr_b300.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -413,7 +413,7 @@ template <class E>
 int check_kernel(hpr_ctx *ctx)
 {
     int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sell<E>, TB, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sell<E>, SELL_TB, 0));
     if (per_sm < 1) return fail_arg(ctx, HPR_ERR_CUDA, "sliced-ELL kernel does not fit on an SM");
     return HPR_OK;
 }
@@ -422,7 +422,7 @@ template <class E>
 int launch_sell(hpr_ctx *ctx, const SellDev &M, const E &e, const int *skip = nullptr)
 {
     if (M.rows == 0) return HPR_OK;
-    k_sell<E><<<M.grid, TB, 0, ctx->stream>>>(sell_of(M, sizeof(typename E::Val) == 4, skip), e);
+    k_sell<E><<<M.grid, SELL_TB, 0, ctx->stream>>>(sell_of(M, sizeof(typename E::Val) == 4, skip), e);
     CKL();
     ctx->launches += 1;
     return HPR_OK;
@@ -439,7 +439,7 @@ int launch_sell_pdl(hpr_ctx *ctx, const SellDev &M, const E &e)
     a.trigger_from = std::max(0, M.grid - SELL_CTAS_PER_SM * ctx->num_sms);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)M.grid);
-    cfg.blockDim = dim3(TB);
+    cfg.blockDim = dim3(SELL_TB);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr[1];
@@ -718,7 +718,7 @@ int install_layout(hpr_ctx *ctx, SellDev &D, const SellHost &H, int rows, const 
     D.steps_max = H.steps_max; D.unit_cost = H.unit_cost;
     D.nruns = (int)H.wstart.size() - 1;
     D.ucost = H.ucost;
-    D.grid = std::max(1, (D.nruns + TB / 32 - 1) / (TB / 32));
+    D.grid = std::max(1, (D.nruns + SELL_WARPS - 1) / SELL_WARPS);
     D.entries = (int64_t)H.col.size();
     DALLOC(D.val32, D.entries);
     DALLOC(D.srow, (int64_t)H.srow.size()); DALLOC(D.sptr, (int64_t)H.sptr.size());
@@ -886,15 +886,15 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
         if ((r = check_kernel<EpiY32<true>>(ctx))) return r;
     }
     const int unitsA = (int)hA.wstart.size() - 1, unitsT = (int)hT.wstart.size() - 1;
-    const int gA = std::max(1, (unitsA + TB / 32 - 1) / (TB / 32));
-    const int gT = std::max(1, (unitsT + TB / 32 - 1) / (TB / 32));
+    const int gA = std::max(1, (unitsA + SELL_WARPS - 1) / SELL_WARPS);
+    const int gT = std::max(1, (unitsT + SELL_WARPS - 1) / SELL_WARPS);
     ctx->pstride = std::max({gA, gT, (int)((std::max(m, n) + TB - 1) / TB), 1});
     auto upload_sell = [&](SellDev &D, const SellHost &H, int rows) -> int {
         D.rows = rows; D.nslices = H.nslices;
         D.steps_max = H.steps_max; D.unit_cost = H.unit_cost;
         D.nruns = (int)H.wstart.size() - 1;
         D.ucost = H.ucost;
-        D.grid = std::max(1, (D.nruns + TB / 32 - 1) / (TB / 32));
+        D.grid = std::max(1, (D.nruns + SELL_WARPS - 1) / SELL_WARPS);
         D.entries = (int64_t)H.col.size();
         DALLOC(D.val32, D.entries);
         DALLOC(D.srow, (int64_t)H.srow.size()); DALLOC(D.sptr, (int64_t)H.sptr.size());
@@ -1988,7 +1988,7 @@ int upload_table(const std::vector<T> &h, T **d)
 }
 
 // fused CTA list of one phase: every CTA of every context's own launch, costliest first
-// (cost: its 8 work units), ties by context and CTA
+// (cost: its SELL_WARPS work units), ties by context and CTA
 std::vector<MultiTask> fused_tasks(const std::vector<hpr_ctx *> &cs, bool transpose)
 {
     struct T { float cost; int inst, cta; };
@@ -1998,7 +1998,7 @@ std::vector<MultiTask> fused_tasks(const std::vector<hpr_ctx *> &cs, bool transp
         if (M.rows == 0) continue;
         for (int c = 0; c < M.grid; ++c) {
             float cost = 0.f;
-            for (int r = c * (TB / 32); r < std::min(M.nruns, (c + 1) * (TB / 32)); ++r) cost += M.ucost[(size_t)r];
+            for (int r = c * SELL_WARPS; r < std::min(M.nruns, (c + 1) * SELL_WARPS); ++r) cost += M.ucost[(size_t)r];
             all.push_back({cost, (int)i, c});
         }
     }
@@ -2069,7 +2069,7 @@ template <class E, int MODE, int FORM>
 int launch_multi(hpr_batch *b, const MultiTask *tasks, int ntasks, const SellArgs *sells, const E *epis, int it)
 {
     if (ntasks == 0) return HPR_OK;
-    k_sell_multi<E, MODE, FORM><<<ntasks, TB, 0, b->stream>>>(tasks, sells, epis, it);
+    k_sell_multi<E, MODE, FORM><<<ntasks, SELL_TB, 0, b->stream>>>(tasks, sells, epis, it);
     if (cudaGetLastError() != cudaSuccess) return HPR_ERR_CUDA;
     b->fused_launches += 1;
     return HPR_OK;

@@ -23,10 +23,18 @@
 
 namespace hprdev {
 
-constexpr int TB = 256;                 // threads per CTA
-#ifndef HPR_SELL_CTAS
-#define HPR_SELL_CTAS 4
+constexpr int TB = 256;                 // threads per CTA (vector, reduction kernels)
+#ifndef HPR_SELL_TB
+#define HPR_SELL_TB 64
 #endif
+#ifndef HPR_SELL_CTAS
+#define HPR_SELL_CTAS 16
+#endif
+// The sliced-ELL kernels run small CTAs: one work unit per warp, 2 warps per CTA, so the
+// hardware block scheduler balances the units' uneven costs at a fine grain and a CTA
+// whose warps finish early frees its slot at once.
+constexpr int SELL_TB = HPR_SELL_TB;             // threads per sliced-ELL CTA
+constexpr int SELL_WARPS = SELL_TB / 32;         // work units per sliced-ELL CTA
 constexpr int SELL_CTAS_PER_SM = HPR_SELL_CTAS;  // resident CTAs of the sliced-ELL kernels
 
 // quantities reduced at a check (indices into the partials / scalar arrays)
@@ -68,10 +76,12 @@ struct PowCtl {
 };
 
 // ------------------------------------------------------------------ block reduction
-// Fixed-order sum of one double per thread over a TB-thread block; result valid in
-// thread 0.  Order: xor-butterfly inside each warp, then the 8 warp sums in order.
-__device__ __forceinline__ double block_sum(double v, double *scratch /* >= TB/32 */)
+// Fixed-order sum of one double per thread over an NT-thread block; result valid in
+// thread 0.  Order: xor-butterfly inside each warp, then the NT/32 warp sums in order.
+template <int NT = TB>
+__device__ __forceinline__ double block_sum(double v, double *scratch /* >= NT/32 */)
 {
+    static_assert(NT % 32 == 0 && NT >= 32, "whole warps");
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -82,7 +92,7 @@ __device__ __forceinline__ double block_sum(double v, double *scratch /* >= TB/3
     if (threadIdx.x == 0) {
         s = scratch[0];
 #pragma unroll
-        for (int i = 1; i < TB / 32; ++i) s += scratch[i];
+        for (int i = 1; i < NT / 32; ++i) s += scratch[i];
     }
     return s;
 }
@@ -323,14 +333,14 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
 }
 
 template <class E>
-__global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
+__global__ void __launch_bounds__(SELL_TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
 {
     constexpr int NP = E::NP;
-    __shared__ double red[TB / 32];
+    __shared__ double red[SELL_WARPS];
     if (S.skip && *S.skip) return;
     E ee = e;
     ee.load();
-    const int run = blockIdx.x * (TB / 32) + (threadIdx.x >> 5);   // one unit per warp
+    const int run = blockIdx.x * SELL_WARPS + (threadIdx.x >> 5);   // one unit per warp
     double part[NP > 0 ? NP : 1];
 #pragma unroll
     for (int i = 0; i < (NP > 0 ? NP : 1); ++i) part[i] = 0.0;
@@ -338,15 +348,15 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell(SellArgs S, E e)
     if (NP > 0) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-            const double t = block_sum(part[i], red);
+            const double t = block_sum<SELL_TB>(part[i], red);
             if (threadIdx.x == 0) ee.partials[ee.q[i] * ee.pstride + blockIdx.x] = t;
         }
     }
 }
 
 // Many LPs in one launch (the batched solve).  Block b of a fused launch is CTA
-// tasks[b].cta of context tasks[b].inst: its 8 warps take that context's work units
-// 8 cta .. 8 cta + 7, exactly as block `cta` of the context's own launch would, so the
+// tasks[b].cta of context tasks[b].inst: its SELL_WARPS warps take that context's work
+// units SELL_WARPS cta + w, exactly as block `cta` of the context's own launch would, so the
 // per-row arithmetic and the per-CTA partial sums are the same.  The context's layout
 // and epilogue operands come from per-context tables.  A whole block skips unless its
 // context is active, in the form FORM (-1: any), and iteration `it` is one this launch
@@ -363,13 +373,13 @@ __device__ __forceinline__ bool multi_runs(const DevCtl *c, int mode, int form, 
 }
 
 template <class E, int MODE, int FORM>
-__global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell_multi(const MultiTask *__restrict__ tasks,
+__global__ void __launch_bounds__(SELL_TB, SELL_CTAS_PER_SM) k_sell_multi(const MultiTask *__restrict__ tasks,
                                                                   const SellArgs *__restrict__ sells,
                                                                   const E *__restrict__ epis, int it)
 {
     constexpr int NP = E::NP;
     static_assert(MODE == 1 || NP == 0, "normal iterations have no partial sums");
-    __shared__ double red[TB / 32];
+    __shared__ double red[SELL_WARPS];
     const MultiTask t = tasks[blockIdx.x];
     E ee = epis[t.inst];
     if (!multi_runs(ee.ctl, MODE, FORM, it)) return;        // the whole block
@@ -379,11 +389,11 @@ __global__ void __launch_bounds__(TB, SELL_CTAS_PER_SM) k_sell_multi(const Multi
     double part[NP > 0 ? NP : 1];
 #pragma unroll
     for (int i = 0; i < (NP > 0 ? NP : 1); ++i) part[i] = 0.0;
-    sell_unit(S, ee, t.cta * (TB / 32) + (threadIdx.x >> 5), part);
+    sell_unit(S, ee, t.cta * SELL_WARPS + (threadIdx.x >> 5), part);
     if (NP > 0) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-            const double s = block_sum(part[i], red);
+            const double s = block_sum<SELL_TB>(part[i], red);
             if (threadIdx.x == 0) ee.partials[ee.q[i] * ee.pstride + t.cta] = s;
         }
     }
