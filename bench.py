@@ -32,9 +32,9 @@ METRIC = ("time-to-KKT≤1e-8 (s), HPR iters/s, HBM GB/s % of peak; chosen form 
 # DRAM bytes per launch from one ncu capture of the full-size workload (see
 # profiles/), valid only for the kernel source they were taken on.
 NCU_TRAFFIC = {
-    "source_sha1": "2e8c1e034f8f75faea8043e4dc179a8385a6aebf",
-    "k_phase_x": 87655168,
-    "k_phase_y": 73297152,
+    "source_sha1": "20c28fd31299cfc25da142959919d90d53146536",
+    "k_phase_x": 87993600,
+    "k_phase_y": 73059584,
 }
 
 
