@@ -170,11 +170,15 @@ def workload(args):
         return lpgen.mcf_lp(args.seed, nodes=max(2, int(round(1_000_000 * args.scale))))
     if args.workload == "qap":
         return lpgen.qap_lp(args.seed, args.qap_n)
+    if args.workload == "tiny":
+        return lpgen.planted_tiny(args.seed)
     return lpgen.planted_medium(args.seed, args.scale)
 
 
 def config_dict(args, lp):
-    if args.workload == "qap":
+    if args.workload == "tiny":
+        name = f"tiny planted LP (m={lp.m}, m1={lp.m1}, n={lp.n}, nnz={lp.nnz}, seed {args.seed})"
+    elif args.workload == "qap":
         name = (f"QAP LP, Adams-Johnson linearisation, random flows and grid distances, N={args.qap_n} "
                 f"(m={lp.m}, n={lp.n}, nnz={lp.nnz}, seed {args.seed})")
     elif args.workload == "mcf":
@@ -490,6 +494,97 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_tiny(args):
+    """Tiny planted LPs (m = 100, n = 200, nnz ~ 1,000; seeds seed .. seed + count - 1), each
+    solved to tol on the default path (the persistent single-CTA kernel) and on the
+    multi-CTA graph path: median time to KKT <= tol and <= 1e-4 (power method included) and
+    microseconds per iteration; value = iterations / s of the default path over all LPs.
+    e2e: one-shot solves through the C ABI from host arrays (create, upload, scaling,
+    solve, download)."""
+    import numpy as np
+    import torch
+
+    from paper_2408_12179_b300 import hpr, lpgen
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    hpr.load()
+    stream = torch.cuda.Stream()
+    lps = [lpgen.planted_tiny(s) for s in range(args.seed, args.seed + args.count)]
+    res = {}
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    for path, p in (("single_cta", 1), ("multi_cta", 0)):
+        rows = []
+        for lp in lps:
+            with hpr.Solver(lp, max_iter=args.max_iter, cuda_stream=stream.cuda_stream, persistent=p) as s:
+                for _ in range(args.warmup):
+                    s.solve(args.tol)
+                torch.cuda.synchronize()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                infos = [s.solve(args.tol)["info"] for _ in range(args.steps)]
+                ev1.record(stream)
+                torch.cuda.synchronize()
+            secs = ev0.elapsed_time(ev1) / 1e3 / args.steps
+            I = infos[-1]
+            rows.append(dict(secs=secs, iters=int(I["iters"]), t4=I["time_to_1e4_s"], power=I["power_time_s"],
+                             launches=int(I["launches"]), status=int(I["status"])))
+        res[path] = rows
+    clocks = sampler.stop()
+
+    def summary(rows):
+        return {"time_to_kkt_1e-8_s_median": statistics.median(r["secs"] for r in rows),
+                "time_to_kkt_1e-4_s_median": statistics.median(r["t4"] for r in rows),
+                "power_method_s_median": statistics.median(r["power"] for r in rows),
+                "us_per_iter": 1e6 * sum(r["secs"] for r in rows) / sum(r["iters"] for r in rows),
+                "launches_per_solve": statistics.median(r["launches"] for r in rows),
+                "all_ok": all(r["status"] == 0 for r in rows)}
+
+    single = res["single_cta"]
+    total_iters = sum(r["iters"] for r in single)
+    total_secs = sum(r["secs"] for r in single)
+    # end to end from host arrays
+    h2d = sum((lp.A1.indptr.size + lp.A2.indptr.size) * 8 + lp.nnz * 12 + lp.m * 8 + lp.n * 24 for lp in lps)
+    d2h = sum((2 * lp.n + lp.m) * 8 for lp in lps)
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for lp in lps:
+        e2e_iters += hpr.solve(lp, tol=args.tol, max_iter=args.max_iter, cuda_stream=stream.cuda_stream)["info"]["iters"]
+    torch.cuda.synchronize()
+    e2e_secs = time.perf_counter() - t0
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        t0 = time.perf_counter()
+        o_iters = 0
+        for lp in lps:
+            o_iters += oracle.solve(lp, tol=args.tol, max_iter=args.max_iter)["info"]["iters"]
+        o_secs = time.perf_counter() - t0
+        cpu = {"value": o_iters / o_secs, "unit": "iter/s",
+               "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+               "sample": f"full solves to tol of the same {len(lps)} LPs (power method included)"}
+    line = {
+        "metric": METRIC, "value": total_iters / total_secs, "unit": "iter/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_secs,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": (f"tiny planted LPs (m=100, m1=40, n=200, nnz ~1000, entries N(0,1) with "
+                                f"p=0.05), seeds {args.seed}..{args.seed + len(lps) - 1}"),
+                   "count": len(lps), "tol": args.tol,
+                   "l2": "working set far below L2 (latency-bound; no flush)"},
+        "single_cta": summary(single), "multi_cta": summary(res["multi_cta"]),
+        "gpu_launches": int(sum(r["launches"] for r in single)) * args.steps,
+        "e2e": {"value": e2e_iters / e2e_secs, "unit": "iter/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_secs},
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -507,11 +602,12 @@ def main():
                     help="0: FP64; 1: FP32 form, then FP64 below KKT 1e-5")
     ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true",
                     help="also time one plain FP64 solve and report it beside the chosen form")
-    ap.add_argument("--workload", choices=["medium", "mcf", "batch", "qap"], default="medium",
+    ap.add_argument("--workload", choices=["medium", "mcf", "batch", "qap", "tiny"], default="medium",
                     help="medium sparse planted LP (default), the min-cost multicommodity flow LP "
                          "(1M nodes at scale 1), or a batch of uneven planted LPs solved in one "
                          "batched run (m log-uniform in [500, 50000 * scale])")
-    ap.add_argument("--count", type=int, default=512, help="LPs in the batch workload")
+    ap.add_argument("--count", type=int, default=None,
+                    help="LPs in the batch workload (default 512) or the tiny workload (default 10)")
     ap.add_argument("--qap-n", dest="qap_n", type=int, default=30,
                     help="QAP workload: N (N^4 + N^2 variables)")
     ap.add_argument("--autotune", action="store_true",
@@ -524,7 +620,11 @@ def main():
     ap.add_argument("--lambda-fixed", dest="lambda_fixed", type=float, default=0.0,
                     help="use this lambda instead of the power method (short profiling runs)")
     args = ap.parse_args()
-    if args.impl == "reference" and args.workload == "batch":
+    if args.count is None:
+        args.count = 10 if args.workload == "tiny" else 512
+    if args.workload == "tiny" and args.impl == "ours":
+        run_tiny(args)
+    elif args.impl == "reference" and args.workload == "batch":
         run_reference_batch(args)
     elif args.workload == "batch":
         run_batch(args)

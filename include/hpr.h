@@ -119,9 +119,12 @@ typedef struct {
                                  (log10 KKT units; default 0) */
     int64_t persistent;       /* the persistent single-CTA path: one CTA of 1024 threads runs the
                                  power method and all of Algorithm 2 on the device, iterates in
-                                 shared memory (LPs with 56 n + 48 m bytes <= 200 KB).  0 never;
-                                 1 (default) when the LP fits and the solve is plain FP64 without
-                                 tracing, time limit or policy; 2 always (HPR_ERR_ARG if it cannot) */
+                                 shared memory (LPs with 48 n + 32 m bytes <= 200 KB).  0 never;
+                                 1 (default) when the LP fits, the solve is plain FP64 without
+                                 tracing, time limit or policy, and one SM's share of FP64 work per
+                                 iteration is small enough to beat the multi-CTA path (stored
+                                 entries of A and A^T / 32 + 8 x their 32-row slices <= 600);
+                                 2 whenever it can run (HPR_ERR_ARG if it cannot) */
     int64_t pdl;              /* 1 (default): the two phases of a normal iteration are launched as
                                  programmatic dependents of the kernel before them, so that their
                                  set-up overlaps its tail; 0: plain stream order */

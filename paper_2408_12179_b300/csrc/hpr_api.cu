@@ -1619,17 +1619,31 @@ int solve_finish(hpr_ctx *ctx)
 }
 
 constexpr size_t SMALL_SMEM_MAX = 200 * 1024;
+// One SM issues the FP64 work of the whole iteration: about one warp instruction per 32
+// stored entries of A and A^T plus ~8 per 32-row slice (row sums' tails and epilogues), at
+// ~17 cycles each.  Measured on the tiny planted LP, QAPs (N = 5, 6) and medium planted LPs
+// at 1/1000 .. 1/200 scale, an iteration of the single CTA costs ~1.5 us + 8.4 ns per such
+// instruction, and the multi-CTA graph path ~5 us (launch-bound) or more; the default takes
+// the single CTA up to 600 instructions (~6.5 us).
+constexpr double SMALL_FP64_MAX = 600.0;
 
-// whether the persistent single-CTA path can run this solve (and why not)
-const char *small_unfit(const hpr_ctx *ctx)
+double small_fp64_per_iter(const hpr_ctx *ctx)
+{
+    return (double)(ctx->SA.entries + ctx->ST.entries) / 32.0 + 8.0 * (double)(ctx->SA.nslices + ctx->ST.nslices);
+}
+
+// whether the persistent single-CTA path can run this solve (and why not); unless forced,
+// also whether it is expected to be the faster path
+const char *small_unfit(const hpr_ctx *ctx, bool forced)
 {
     const hpr_options &o = ctx->opt;
-    if (hprsmall::small_smem_bytes((int)ctx->m, (int)ctx->n, ctx->nnz, false) > SMALL_SMEM_MAX)
+    if (hprsmall::small_vec_bytes((int)ctx->m, (int)ctx->n) > SMALL_SMEM_MAX)
         return "the iterates do not fit in shared memory";
     if (o.precision != 0) return "the FP32 form";
     if (o.trace_iters > 0) return "tracing";
     if (o.time_limit_s > 0.0) return "a time limit";
     if (o.sigma_policy != 0) return "a sigma policy";
+    if (!forced && small_fp64_per_iter(ctx) > SMALL_FP64_MAX) return "more FP64 work per iteration than one SM takes faster";
     return nullptr;
 }
 
@@ -1659,11 +1673,17 @@ int solve_small(hpr_ctx *ctx, double tol)
     if (!ctx->small_out) DALLOC(ctx->small_out, SO_LEN);
     hpr_check_record *recs = ctx->small_recs;
     double *out = ctx->small_out;
+    auto mat_of = [](const SellDev &D) {
+        SmallMat M{};
+        M.nslices = D.nslices; M.entries = D.entries;
+        M.srow = D.srow; M.sptr = D.sptr; M.col = D.col; M.slg = D.slg; M.val = D.val;
+        return M;
+    };
     SmallArgs A{};
-    A.m = (int)m; A.m1 = (int)ctx->m1; A.n = (int)n;
-    A.rp = ctx->A_rp; A.ci = ctx->A_ci; A.val = ctx->A_val;
-    A.trp = ctx->T_rp; A.tci = ctx->T_ci; A.tval = ctx->T_val;
-    A.b = ctx->b_s; A.c = ctx->c_s; A.l = ctx->l_s; A.u = ctx->u_s; A.wr = ctx->wr; A.wc = ctx->wc;
+    A.m = (int)m; A.n = (int)n;
+    A.A = mat_of(ctx->SA); A.T = mat_of(ctx->ST);
+    A.ineq = ctx->ineq;
+    A.b = ctx->bp; A.c = ctx->cp; A.l = ctx->lp; A.u = ctx->up; A.wr = ctx->wrp; A.wc = ctx->wcp;
     A.beta_b = ctx->beta_b; A.beta_c = ctx->beta_c; A.norm_b = ctx->norm_b; A.norm_c = ctx->norm_c;
     A.tol = tol; A.alpha1 = o.alpha1; A.alpha2 = o.alpha2; A.alpha3 = o.alpha3; A.sigma0 = o.sigma0;
     A.lambda_fixed = o.lambda_fixed; A.power_tol = o.power_tol;
@@ -1671,22 +1691,11 @@ int solve_small(hpr_ctx *ctx, double tol)
     A.seed = o.seed;
     A.restart = (int)o.restart; A.sigma_update = (int)o.sigma_update; A.halpern = (int)o.halpern;
     A.reflect = (int)o.reflect;
-    // lanes per row: the largest power of two (<= 32, <= the mean row length) that still gives
-    // every row its lanes in one pass
-    auto lanes = [&](int64_t rows) {
-        const double mean = (double)ctx->nnz / (double)std::max<int64_t>(rows, 1);
-        int L = 1;
-        while (L < 32 && (int64_t)(2 * L) * rows <= NT && 2 * L <= mean) L *= 2;
-        return L;
-    };
-    A.LA = lanes(m);
-    A.LT = lanes(n);
-    A.nnz = (int)ctx->nnz;
-    A.mat_smem = small_smem_bytes((int)m, (int)n, ctx->nnz, true) <= SMALL_SMEM_MAX ? 1 : 0;
-    A.perm_r = ctx->perm_r; A.perm_c = ctx->perm_c;
+    A.mat_smem = small_smem_bytes((int)m, (int)n, A.A, A.T, true) <= SMALL_SMEM_MAX ? 1 : 0;
+    A.perm_r = ctx->perm_r;
     A.xbar_out = ctx->xbar; A.ybar_out = ctx->ybar; A.zbar_out = ctx->zbar;
     A.recs = recs; A.rec_cap = cap; A.out = out;
-    const size_t smem = small_smem_bytes((int)m, (int)n, ctx->nnz, A.mat_smem != 0);
+    const size_t smem = small_smem_bytes((int)m, (int)n, A.A, A.T, A.mat_smem != 0);
     int st = HPR_OK;
     cudaError_t e = cudaFuncSetAttribute(k_solve_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
@@ -1732,7 +1741,7 @@ int hpr_solve(hpr_ctx *ctx, double tol)
     if (ctx->batched) return fail_arg(ctx, HPR_ERR_STATE, "the context belongs to a batch");
     cudaSetDevice(ctx->device);
     if (ctx->opt.persistent) {
-        const char *why = small_unfit(ctx);
+        const char *why = small_unfit(ctx, ctx->opt.persistent == 2);
         if (!why) return solve_small(ctx, tol);
         if (ctx->opt.persistent == 2)
             return fail_arg(ctx, HPR_ERR_ARG, std::string("persistent = 2 but the single-CTA path cannot run: ") + why);

@@ -101,3 +101,21 @@ def test_persistent_is_faster_per_iteration():
         out[p] = 1e6 * I["solve_time_s"] / I["iters"]
     print(f"us per iteration: multi-CTA graph path {out[0]:.2f}, single CTA {out[2]:.2f}")
     assert out[2] < out[0]
+
+
+def test_default_path_choice():
+    """persistent = 1 takes the single CTA for the tiny planted LP and the multi-CTA path for a
+    medium planted LP at 1/200 scale, whose iterates fit in shared memory but whose FP64 work
+    per iteration is beyond what one SM does faster; persistent = 2 still runs it in one CTA,
+    to the same result as the multi-CTA path."""
+    lp = lpgen.planted_medium(0, 0.005)
+    with hpr.Solver(lpgen.planted_tiny(0), persistent=1) as s:
+        assert s.solve(1e-8)["info"]["launches"] <= 3
+    res = {}
+    for p in (1, 2):
+        with hpr.Solver(lp, persistent=p, max_iter=1500) as s:
+            r = s.solve(1e-8)
+        assert (r["info"]["launches"] <= 3) == (p == 2)
+        res[p] = r
+    assert res[1]["info"]["iters"] == res[2]["info"]["iters"] == 1500
+    assert res[2]["info"]["kkt"] == pytest.approx(res[1]["info"]["kkt"], rel=1e-3)
