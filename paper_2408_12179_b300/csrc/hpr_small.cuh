@@ -132,64 +132,95 @@ __device__ __forceinline__ void cta_sums(double (&v)[NV], int nact, double *red,
     __syncthreads();
 }
 
-__device__ __forceinline__ double cta_sum1(double v, int nact, double *red, double *outv)
+// The same fixed-order sums, handed to g(sums) on thread 0 before the closing barrier: g
+// takes a decision and publishes it through shared memory, so that no other warp spends
+// FP64 issue slots on it.
+template <int NV, class G>
+__device__ __forceinline__ void cta_sums_then(double (&v)[NV], int nact, double *red, G g)
 {
-    double a[1] = {v};
-    cta_sums<1>(a, nact, red, outv);
-    return outv[0];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < nact) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) red[q * 32 + w] = v[q];
+        }
+    }
+    __syncthreads();
+    if (w == 0) {
+        double sum[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = lane < nact ? red[q * 32 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            sum[q] = t;
+        }
+        if (lane == 0) g(static_cast<const double *>(sum));
+    }
+    __syncthreads();
 }
 
 // power method on A A^* (Section 4.1): u0 from SplitMix64(seed) at each row's original
 // index, normalised; s = A^T u, lambda = ||s||^2, stop when |lambda_k - lambda_{k-1}| <=
-// tol lambda_k or after power_max_iter steps; u = A s / ||A s||.  u, w (m) and s (n) are
-// shared-memory scratch; sc is shared scratch for the broadcast scalars.
-__device__ double power_small(const SmallArgs &P, double *u, double *w, double *s, double *red, double *sc,
+// tol lambda_k or after power_max_iter steps; u = A s / ||A s||.  w (m, u unnormalised) and
+// s (n) are shared-memory scratch; sc holds the broadcast scalars.  A step computes
+// s = (A^T w) / ||w|| (the normalisation applied in the row sums) and w' = A s, then sums
+// ||s||^2 and ||w'||^2 in one reduction whose thread 0 takes the decisions: three barriers
+// a step and no FP64 work outside the warps that own rows.  (The last step's A s is not
+// needed; it keeps the step uniform.)
+__device__ double power_small(const SmallArgs &P, double *w, double *s, double *red, double *sc, int *flag,
                               int64_t *iters)
 {
     const int tid = threadIdx.x;
     const int act_m = owner_warps((P.m + 31) / 32), actA = owner_warps(P.A.nslices),
               actT = owner_warps(P.T.nslices);
-    double p = 0.0;
+    double p[2] = {0.0, 0.0};
     for (int i = tid; i < P.m; i += NT) {
         const uint64_t o = (uint64_t)P.perm_r[i];
         const double v = 2.0 * ((double)(hprdev::splitmix64_at(P.seed, o) >> 11) * 0x1.0p-53) - 1.0;
-        u[i] = v;
-        p = fma(v, v, p);
+        w[i] = v;
+        p[0] = fma(v, v, p[0]);
     }
-    cta_sum1(p, act_m, red, sc);
-    if (tid == 0) {                      // one thread (inputs reloaded through volatile shared memory so
-        const double v = ((volatile double *)sc)[0];     // that the costly FP64 divide and root are
-        sc[1] = 1.0 / sqrt(v);                           // not replicated into every thread)
+    // sc[0]: 1 / ||w||, sc[1]: lambda_k; flag: stop
+    cta_sums<2>(p, act_m, red, sc);
+    if (tid == 0) {
+        sc[0] = 1.0 / sqrt(((volatile double *)sc)[0]);
+        *flag = 0;
     }
     __syncthreads();
-    const double inv0 = sc[1];
-    for (int i = tid; i < P.m; i += NT) u[i] *= inv0;
-    __syncthreads();
-    double lam = 0.0, lam_prev = 0.0;
+    const int act = actA > actT ? actA : actT;
+    double lam = 0.0;
     int64_t k = 0;
     for (;;) {
-        double q = 0.0;
-        sell_rows(P.T, u, [&](int j, double sj) {
-            s[j] = sj;
-            q = fma(sj, sj, q);
+        const double inv = sc[0];
+        double q[2] = {0.0, 0.0};
+        sell_rows(P.T, w, [&](int j, double sj) {
+            const double t = sj * inv;
+            s[j] = t;
+            q[0] = fma(t, t, q[0]);
         });
-        lam = cta_sum1(q, actT, red, sc);       // (its barriers also publish s)
-        ++k;
-        if (k > 1 && fabs(lam - lam_prev) <= P.power_tol * lam) break;
-        lam_prev = lam;
-        double q2 = 0.0;
+        __syncthreads();
         sell_rows(P.A, s, [&](int i, double wi) {
             w[i] = wi;
-            q2 = fma(wi, wi, q2);
+            q[1] = fma(wi, wi, q[1]);
         });
-        const double w2 = cta_sum1(q2, actA, red, sc);
-        if (!(w2 > 0.0) || k >= P.power_max_iter) break;
-        if (tid == 0) sc[1] = 1.0 / sqrt(((volatile double *)sc)[0]);
-        __syncthreads();
-        const double inv = sc[1];
-        for (int i = tid; i < P.m; i += NT) u[i] = w[i] * inv;
-        __syncthreads();
+        ++k;
+        cta_sums_then<2>(q, act, red, [&](const double *sum) {
+            const double l = sum[0], prev = sc[1];
+            sc[1] = l;
+            if ((k > 1 && fabs(l - prev) <= P.power_tol * l) || k >= P.power_max_iter || !(sum[1] > 0.0))
+                *flag = 1;
+            else
+                sc[0] = 1.0 / sqrt(sum[1]);
+        });
+        if (*flag) break;
     }
+    lam = sc[1];
     *iters = k;
     return lam;
 }
@@ -259,6 +290,7 @@ __global__ void __launch_bounds__(NT) k_solve_small(SmallArgs P)
     __shared__ double red[10 * 32];
     __shared__ double sums[10];
     __shared__ double sc[2];
+    __shared__ int pflag;
     __shared__ double sc_in[2];
     __shared__ double bc_sigma, bc_ha, bc_hb, bc_ils;    // this iteration's scalars (thread 0 sets them)
     __shared__ int bc_restart, bc_stop;
@@ -267,7 +299,7 @@ __global__ void __launch_bounds__(NT) k_solve_small(SmallArgs P)
     // ---- lambda of T1 = lambda I - A A^* (power method, counted in the solve time)
     double lambda = P.lambda_fixed;
     int64_t piters = 0;
-    if (!(lambda > 0.0)) lambda = power_small(P, y, yb, x, red, sc, &piters);
+    if (!(lambda > 0.0)) lambda = power_small(P, yb, x, red, sc, &pflag, &piters);
     const uint64_t t_power = now_ns();
 
     // ---- origin start, sigma_0 (Section 4.1)
