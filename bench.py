@@ -29,8 +29,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("time-to-KKT≤1e-8 (s), HPR iters/s, HBM GB/s % of peak; chosen form vs plain FP64")
 
-# DRAM bytes per launch from one ncu capture of the full-size workload (see
-# profiles/), valid only for the kernel source they were taken on.
+# DRAM bytes per launch from one ncu capture of the medium planted LP (seed 0, full size,
+# FP64; see profiles/), valid only for that workload and the kernel source they were
+# taken on.
 NCU_TRAFFIC = {
     "source_sha1": "20c28fd31299cfc25da142959919d90d53146536",
     "k_phase_x": 87993600,
@@ -407,8 +408,9 @@ def run_ours(args):
     dom, dom_ms, dom_bytes = ("k_phase_x", ms_x, bx) if ms_x >= ms_y else ("k_phase_y", ms_y, by)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     traffic = None
-    if NCU_TRAFFIC["source_sha1"] == kernel_source_sha1():
-        traffic = NCU_TRAFFIC.get(dom)
+    if (NCU_TRAFFIC["source_sha1"] == kernel_source_sha1() and args.workload == "medium" and args.scale == 1.0
+            and args.seed == 0 and args.precision == 0 and args.variant == "hpr"):
+        traffic = NCU_TRAFFIC.get(dom)          # captured on this workload only
     iter_gbs = (bx + by) / (ms_it * 1e-3) / 1e9
     plain = None
     if args.compare_fp64 and args.precision != 0:
@@ -535,10 +537,12 @@ def run_tiny(args):
     clocks = sampler.stop()
 
     def summary(rows):
+        its = sum(r["iters"] for r in rows)
         return {"time_to_kkt_1e-8_s_median": statistics.median(r["secs"] for r in rows),
                 "time_to_kkt_1e-4_s_median": statistics.median(r["t4"] for r in rows),
                 "power_method_s_median": statistics.median(r["power"] for r in rows),
-                "us_per_iter": 1e6 * sum(r["secs"] for r in rows) / sum(r["iters"] for r in rows),
+                "us_per_iter_with_power_method": 1e6 * sum(r["secs"] for r in rows) / its,
+                "us_per_iter": 1e6 * sum(r["secs"] - r["power"] for r in rows) / its,
                 "launches_per_solve": statistics.median(r["launches"] for r in rows),
                 "all_ok": all(r["status"] == 0 for r in rows)}
 
