@@ -102,9 +102,12 @@ typedef struct {
                                  the layouts given below */
     int64_t sell_steps_a, sell_steps_t;  /* lanes-per-row bound of A's / A^T's layout: a group
                                  of 32 rows uses the fewest lanes per row (1..32) that keep
-                                 its longest row within this many steps; 0: 40 */
+                                 its longest row within this many steps; 0: 40, or 16 when
+                                 the phase's algorithmic traffic is below 40 MB (the x phase:
+                                 12 nnz + 60 n + 8 m bytes, the y phase: 12 nnz + 8 n + 36 m) */
     double unit_cost_a, unit_cost_t;     /* work-unit size of A's / A^T's layout (a group
-                                 costlier than this is split into one unit per slice); 0: 64 */
+                                 costlier than this is split into one unit per slice); 0: 64,
+                                 or 32 below the same 40 MB */
     int64_t sigma_policy;     /* sigma at a restart where Algorithm 3 computes Delta_x / Delta_y:
                                  0 (default) that value; 1 (exploration, for training data)
                                  2^((a-2)/2) times it with a in 0..4 drawn by SplitMix64 from

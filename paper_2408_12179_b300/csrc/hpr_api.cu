@@ -238,9 +238,13 @@ std::vector<int> order_by_length(const std::vector<int> &rp, int rows)
 // Rows are taken in groups of 32; a group uses L lanes per row, L the smallest power of
 // two that keeps its widest slice within `steps_max` steps (L <= 32), and is stored as L
 // slices of 32 / L rows.  Work units (one per warp): a group whole, or each slice of a
-// group whose cost exceeds `unit_cost`.  Defaults 40 and 64; the autotuner may pick others.
+// group whose cost exceeds `unit_cost`.  Defaults 40 and 64 (16 and 32 for phases below
+// SMALL_PHASE_BYTES); the autotuner may pick others.
 constexpr int SELL_STEPS = 40;
 constexpr double UNIT_COST = 64.0;
+constexpr double SMALL_PHASE_BYTES = 40e6;   // below: SMALL_SELL_STEPS and SMALL_UNIT_COST
+constexpr int SMALL_SELL_STEPS = 16;
+constexpr double SMALL_UNIT_COST = 32.0;
 
 struct SellHost {
     int nslices = 0;
@@ -863,10 +867,17 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     for (int64_t i = 0; i < m; ++i) ipr[(size_t)pr[(size_t)i]] = (int)i;
     for (int64_t j = 0; j < n; ++j) ipc[(size_t)pc[(size_t)j]] = (int)j;
     const hpr_options &op = ctx->opt;
-    const int stepsA = op.sell_steps_a > 0 ? (int)op.sell_steps_a : SELL_STEPS;
-    const int stepsT = op.sell_steps_t > 0 ? (int)op.sell_steps_t : SELL_STEPS;
-    const double costA = op.unit_cost_a > 0.0 ? op.unit_cost_a : UNIT_COST;
-    const double costT = op.unit_cost_t > 0.0 ? op.unit_cost_t : UNIT_COST;
+    // A phase that moves little data is bound by its longest work unit's chain of dependent
+    // loads, not by bandwidth: below SMALL_PHASE_BYTES of algorithmic traffic the default
+    // layout takes shorter slices and smaller units (measured on the QAP LP at N = 20: the
+    // x phase 19.5 -> 10.3 us; the medium LP, at 95 / 74 MB a phase, gains nothing).
+    const double bytesX = 12.0 * (double)nnz + 60.0 * (double)n + 8.0 * (double)m;
+    const double bytesY = 12.0 * (double)nnz + 8.0 * (double)n + 36.0 * (double)m;
+    const bool smallA = bytesY < SMALL_PHASE_BYTES, smallT = bytesX < SMALL_PHASE_BYTES;
+    const int stepsA = op.sell_steps_a > 0 ? (int)op.sell_steps_a : (smallA ? SMALL_SELL_STEPS : SELL_STEPS);
+    const int stepsT = op.sell_steps_t > 0 ? (int)op.sell_steps_t : (smallT ? SMALL_SELL_STEPS : SELL_STEPS);
+    const double costA = op.unit_cost_a > 0.0 ? op.unit_cost_a : (smallA ? SMALL_UNIT_COST : UNIT_COST);
+    const double costT = op.unit_cost_t > 0.0 ? op.unit_cost_t : (smallT ? SMALL_UNIT_COST : UNIT_COST);
     SellHost hA = build_sell(rp, ci, (int)m, pr, ipc, stepsA, costA);
     SellHost hT = build_sell(trp, tci, (int)n, pc, ipr, stepsT, costT);
     std::vector<unsigned char> ineq((size_t)m);

@@ -57,3 +57,18 @@ def test_autotuned_solve_matches_oracle():
     assert ind["kkt"] <= 1e-8 * (1 + 1e-6)
     assert abs(res["info"]["primal_obj"] - ref["info"]["pobj"]) <= 1e-7 * abs(ref["info"]["pobj"])
 
+
+
+@pytest.mark.parametrize("scale", [0.05, 0.5])
+def test_default_layout_follows_phase_traffic(scale):
+    """Without layout options a phase whose algorithmic traffic is below 40 MB gets the
+    short-slice layout (16 steps, units of 32), a larger one the default (40, 64): at half
+    scale the medium LP's x phase (Aᵀ) is above, its y phase (A) below."""
+    lp = lpgen.planted_medium(0, scale)
+    bx = 12 * lp.nnz + 60 * lp.n + 8 * lp.m
+    by = 12 * lp.nnz + 8 * lp.n + 36 * lp.m
+    with hpr.Solver(lp) as s:
+        lay = s.layout()
+    want = lambda b: (16, 32.0) if b < 40e6 else (40, 64.0)
+    assert (lay["sell_steps"][0], lay["unit_cost"][0]) == want(by)
+    assert (lay["sell_steps"][1], lay["unit_cost"][1]) == want(bx)
