@@ -164,6 +164,21 @@ VARIANTS = {
 }
 
 
+def bucket_of(lp):
+    """Size bucket of the batch workload's per-bucket autotuning: floor(log2 nnz)."""
+    return int(math.floor(math.log2(max(lp.nnz, 1))))
+
+
+def layout_opts(args):
+    """Explicit sliced-ELL layout for every context (--sell-steps, --unit-cost), else none."""
+    o = {}
+    if args.sell_steps:
+        o.update(sell_steps_a=args.sell_steps, sell_steps_t=args.sell_steps)
+    if args.unit_cost:
+        o.update(unit_cost_a=args.unit_cost, unit_cost_t=args.unit_cost)
+    return o
+
+
 def workload(args):
     from paper_2408_12179_b300 import lpgen
 
@@ -243,13 +258,14 @@ def run_batch(args):
     lps = lpgen.batch_family(args.seed + rank, args.count, 500, m_hi)
     stream = torch.cuda.Stream()
     opts = dict(tol=args.tol, precision=args.precision, **VARIANTS[args.variant])
+    opts.update(layout_opts(args))
     t_create = time.perf_counter()
     if args.autotune:
         # one autotuned context per size bucket (floor(log2 nnz)); its layout is reused
         tuned = {}
         solvers = []
         for lp in lps:
-            bucket = int(math.floor(math.log2(max(lp.nnz, 1))))
+            bucket = bucket_of(lp)
             if bucket not in tuned:
                 s_ = hpr.Solver(lp, max_iter=args.max_iter, autotune=1, **opts)
                 lay = s_.layout()
@@ -281,21 +297,31 @@ def run_batch(args):
     batch.close()
     conv = [r for r in res if r["status"] == hpr.HPR_OK]
     iters = sum(int(r["info"]["iters"]) for r in res)
-    # the sample: one by one, then as a batch of its own
+    for s_ in solvers:
+        s_.close()
+    # the sample: fresh contexts for the first LPs (the layouts a solo solve gets), solved
+    # one by one (after a warm-up solve each), then as a batch of their own
     k = min(args.solo_sample, len(solvers))
+    sample = [hpr.Solver(lp, max_iter=args.max_iter, **(tuned[bucket_of(lp)] if tuned else {}), **opts)
+              for lp in lps[:k]]
+    for s_ in sample:
+        s_.set_options(max_iter=300)
+        s_.solve(args.tol)
+        s_.set_options(max_iter=args.max_iter)
+    torch.cuda.synchronize()
     t1 = time.perf_counter()
     solo_iters = 0
-    for s_ in solvers[:k]:
+    for s_ in sample:
         solo_iters += int(s_.solve(args.tol)["info"]["iters"])
     torch.cuda.synchronize()
     solo_secs = time.perf_counter() - t1
-    with hpr.Batch(solvers[:k], stream.cuda_stream) as b2:
+    with hpr.Batch(sample, stream.cuda_stream) as b2:
         b2.solve(args.tol)
         t2 = time.perf_counter()
         b2.solve(args.tol)
         torch.cuda.synchronize()
         sample_batch_secs = time.perf_counter() - t2
-    for s_ in solvers:
+    for s_ in sample:
         s_.close()
     if rank != 0:
         return
@@ -310,6 +336,7 @@ def run_batch(args):
                                f"total nnz {nnz}, seed {args.seed})",
                    "tol": args.tol, "max_iter": args.max_iter, "variant": args.variant,
                    "autotune": ({str(k): v for k, v in sorted(tuned.items())} if tuned else None),
+                   "layout": layout_opts(args) or "library default",
                    "create_s": create_secs},
         "batch_status": hpr.hpr_status_str(int(status)), "converged": len(conv), "count": len(lps),
         "time_to_all_s": secs, "iters_summed": iters, "iters_per_s_summed": iters / secs,
@@ -374,6 +401,7 @@ def run_ours(args):
     opts.update(VARIANTS[args.variant])
     if args.autotune:
         opts["autotune"] = 1
+    opts.update(layout_opts(args))
     solver = hpr.Solver(lp, **opts)
     layout = solver.layout()
 
@@ -462,7 +490,7 @@ def run_ours(args):
     t8 = [i["solve_time_s"] for i in infos]
     t4 = [i["time_to_1e4_s"] for i in infos]
     cfg = config_dict(args, lp)
-    if args.autotune:
+    if args.autotune or layout_opts(args):
         cfg["layout"] = layout
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
@@ -614,6 +642,10 @@ def main():
                     help="LPs in the batch workload (default 512) or the tiny workload (default 10)")
     ap.add_argument("--qap-n", dest="qap_n", type=int, default=30,
                     help="QAP workload: N (N^4 + N^2 variables)")
+    ap.add_argument("--sell-steps", dest="sell_steps", type=int, default=0,
+                    help="lanes-per-row bound of both layouts (default: the library's choice)")
+    ap.add_argument("--unit-cost", dest="unit_cost", type=float, default=0.0,
+                    help="work-unit size of both layouts (default: the library's choice)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the sliced-ELL layouts by timing candidates at creation (batch workload: "
                          "once per size bucket of nnz, reused for the bucket's other LPs)")

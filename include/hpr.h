@@ -266,6 +266,11 @@ int hpr_get_layout(const hpr_ctx *ctx, int64_t *sell_steps, double *unit_cost, i
  *                the batch does not own them: destroy the batch first, then the
  *                contexts.  While in the batch a context cannot be solved on its own
  *                (hpr_solve returns HPR_ERR_STATE) and runs on the batch's stream.
+ *                When the contexts' x phases (12 nnz + 60 n + 8 m bytes each) or y phases
+ *                (12 nnz + 8 n + 36 m) add up to 40 MB or more, the fused phase is
+ *                bandwidth-bound and the contexts whose layout took the short-slice
+ *                default for small phases (no layout options, no autotune) get the
+ *                default layout (40, 64) instead, for good (hpr_get_layout shows it).
  *   cuda_stream  the batch's stream (NULL: a stream of its own).
  * hpr_batch_solve returns HPR_OK when every context converged, else the status of a
  * context that did not (HPR_MAX_ITER / HPR_TIME_LIMIT), or an error code; detail in

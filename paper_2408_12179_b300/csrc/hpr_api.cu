@@ -28,6 +28,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <thread>
 #include <type_traits>
 #include <mutex>
@@ -140,6 +141,16 @@ struct hpr_ctx {
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::map<GraphKey, int64_t> graph_launches;   // kernel nodes per captured period
     cudaGraphExec_t pow_graph = nullptr;
+
+    // host structure of the layouts that the small-phase rule gave short slices, kept so
+    // that a batch whose fused phases move enough data can lay them out for throughput
+    // (freed once it has)
+    struct Relayout {
+        bool a = false, t = false;               // A's / A^T's layout took the small-phase rule
+        std::vector<int> rp, ci, pr, ipc;        // A: CSR, row order, column renaming
+        std::vector<int> trp, tci, pc, ipr;      // A^T: the same
+    };
+    std::unique_ptr<Relayout> relayout;
     int64_t launches = 0;                           // kernels launched by the current solve
 
     // results
@@ -822,6 +833,17 @@ int autotune_layout(hpr_ctx *ctx, bool transpose, const std::vector<int> &rp, co
     return HPR_OK;
 }
 
+// algorithmic bytes of the x phase (A^T) and the y phase (A) of one iteration
+double phase_bytes_x(const hpr_ctx *c)
+{
+    return 12.0 * (double)c->nnz + 60.0 * (double)c->n + 8.0 * (double)c->m;
+}
+
+double phase_bytes_y(const hpr_ctx *c)
+{
+    return 12.0 * (double)c->nnz + 8.0 * (double)c->n + 36.0 * (double)c->m;
+}
+
 int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const double *b1,
                        const double *b2, const double *c, const double *l, const double *u)
 {
@@ -871,9 +893,7 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     // loads, not by bandwidth: below SMALL_PHASE_BYTES of algorithmic traffic the default
     // layout takes shorter slices and smaller units (measured on the QAP LP at N = 20: the
     // x phase 19.5 -> 10.3 us; the medium LP, at 95 / 74 MB a phase, gains nothing).
-    const double bytesX = 12.0 * (double)nnz + 60.0 * (double)n + 8.0 * (double)m;
-    const double bytesY = 12.0 * (double)nnz + 8.0 * (double)n + 36.0 * (double)m;
-    const bool smallA = bytesY < SMALL_PHASE_BYTES, smallT = bytesX < SMALL_PHASE_BYTES;
+    const bool smallA = phase_bytes_y(ctx) < SMALL_PHASE_BYTES, smallT = phase_bytes_x(ctx) < SMALL_PHASE_BYTES;
     const int stepsA = op.sell_steps_a > 0 ? (int)op.sell_steps_a : (smallA ? SMALL_SELL_STEPS : SELL_STEPS);
     const int stepsT = op.sell_steps_t > 0 ? (int)op.sell_steps_t : (smallT ? SMALL_SELL_STEPS : SELL_STEPS);
     const double costA = op.unit_cost_a > 0.0 ? op.unit_cost_a : (smallA ? SMALL_UNIT_COST : UNIT_COST);
@@ -1022,6 +1042,56 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
         if (r1) return r1;
         r1 = autotune_layout(ctx, true, trp, tci, pc, ipr);
         if (r1) return r1;
+    } else {
+        const bool ra = smallA && op.sell_steps_a <= 0 && op.unit_cost_a <= 0.0;
+        const bool rt = smallT && op.sell_steps_t <= 0 && op.unit_cost_t <= 0.0;
+        if (ra || rt) {
+            ctx->relayout.reset(new (std::nothrow) hpr_ctx::Relayout());
+            if (!ctx->relayout) return fail_arg(ctx, HPR_ERR_NOMEM, "host copy of the layout structure");
+            hpr_ctx::Relayout &R = *ctx->relayout;
+            R.a = ra;
+            R.t = rt;
+            if (ra) { R.rp = std::move(rp); R.ci = std::move(ci); R.pr = std::move(pr); R.ipc = std::move(ipc); }
+            if (rt) { R.trp = std::move(trp); R.tci = std::move(tci); R.pc = std::move(pc); R.ipr = std::move(ipr); }
+        }
+    }
+    return HPR_OK;
+}
+
+// give a context's short-slice layouts (the small-phase rule) the default layout, for a
+// batch whose fused phases move enough data to be bound by bandwidth, not by the longest
+// unit's latency; captured graphs (they hold the old layouts' pointers) are dropped
+int relayout_for_throughput(hpr_ctx *ctx, bool a, bool t)
+{
+    if (!ctx->relayout) return HPR_OK;
+    hpr_ctx::Relayout &R = *ctx->relayout;
+    a = a && R.a;
+    t = t && R.t;
+    if (!a && !t) return HPR_OK;
+    int st;
+    if (a) {
+        SellHost H = build_sell(R.rp, R.ci, (int)ctx->m, R.pr, R.ipc, SELL_STEPS, UNIT_COST);
+        if ((st = install_layout(ctx, ctx->SA, H, (int)ctx->m, ctx->A_val))) return st;
+        R.a = false;
+        R.rp.clear(); R.ci.clear(); R.pr.clear(); R.ipc.clear();
+    }
+    if (t) {
+        SellHost H = build_sell(R.trp, R.tci, (int)ctx->n, R.pc, R.ipr, SELL_STEPS, UNIT_COST);
+        if ((st = install_layout(ctx, ctx->ST, H, (int)ctx->n, ctx->T_val))) return st;
+        R.t = false;
+        R.trp.clear(); R.tci.clear(); R.pc.clear(); R.ipr.clear();
+    }
+    if (!R.a && !R.t) ctx->relayout.reset();
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+    if (ctx->pow_graph) cudaGraphExecDestroy(ctx->pow_graph);
+    ctx->pow_graph = nullptr;
+    const int need = std::max(ctx->SA.grid, ctx->ST.grid);   // one partial-sum slot per CTA
+    if (need > ctx->pstride) {
+        cudaFree(ctx->partials);
+        ctx->partials = nullptr;
+        ctx->pstride = need;
+        DALLOC(ctx->partials, (int64_t)NQ * ctx->pstride);
     }
     return HPR_OK;
 }
@@ -2166,6 +2236,18 @@ int hpr_batch_create(hpr_batch **out, int64_t count, hpr_ctx *const *ctxs, void 
     }
     for (hpr_ctx *c : cs) cudaStreamSynchronize(c->stream);
     b->ctxs = cs;
+    // a fused phase that moves at least SMALL_PHASE_BYTES in total is bandwidth-bound: the
+    // contexts' short-slice layouts (the small-phase rule) give way to the default layout
+    {
+        double sx = 0.0, sy = 0.0;
+        for (hpr_ctx *c : cs) {
+            sx += phase_bytes_x(c);
+            sy += phase_bytes_y(c);
+        }
+        for (hpr_ctx *c : cs)
+            if (relayout_for_throughput(c, sy >= SMALL_PHASE_BYTES, sx >= SMALL_PHASE_BYTES) != HPR_OK)
+                return fail(HPR_ERR_CUDA, "hpr_batch_create: relayout for throughput failed");
+    }
     std::vector<MultiTask> tT = fused_tasks(cs, true), tA = fused_tasks(cs, false);
     int st = HPR_OK;
     if (cudaMalloc((void **)&b->scal_all, sizeof(double) * 2 * NQ * cs.size()) != cudaSuccess ||

@@ -98,3 +98,28 @@ def test_batch_misuse_is_rejected():
     finally:
         a.close()
         c.close()
+
+
+def test_large_batch_lays_out_small_contexts_for_throughput():
+    """Each LP's phases are small (short-slice layouts by default), but the batch's fused
+    phases move more than 40 MB: the batch gives its contexts the default layout, and its
+    results equal solo solves made with that layout, bit for bit."""
+    lps = [lpgen.planted_medium(seed, 0.1) for seed in range(6)]
+    assert sum(12 * lp.nnz + 60 * lp.n + 8 * lp.m for lp in lps) >= 40e6
+    assert sum(12 * lp.nnz + 8 * lp.n + 36 * lp.m for lp in lps) >= 40e6
+    cap = 600
+    solvers = [hpr.Solver(lp, max_iter=cap) for lp in lps]
+    try:
+        assert all(s.layout()["sell_steps"] == (16, 16) for s in solvers)
+        with hpr.Batch(solvers) as b:
+            assert all(s.layout()["sell_steps"] == (40, 40) for s in solvers)
+            assert all(s.layout()["unit_cost"] == (64.0, 64.0) for s in solvers)
+            status, res = b.solve(1e-8)
+        for lp, r in zip(lps, res):
+            solo = _solo(lp, max_iter=cap, sell_steps_a=40, sell_steps_t=40, unit_cost_a=64.0, unit_cost_t=64.0)
+            assert r["info"]["iters"] == solo["info"]["iters"], lp.name
+            for key in ("x", "y", "z"):
+                assert np.array_equal(r[key], solo[key]), (lp.name, key)
+    finally:
+        for s in solvers:
+            s.close()
