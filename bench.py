@@ -529,8 +529,8 @@ def run_tiny(args):
     solved to tol on the default path (the persistent single-CTA kernel) and on the
     multi-CTA graph path: median time to KKT <= tol and <= 1e-4 (power method included) and
     microseconds per iteration; value = iterations / s of the default path over all LPs.
-    e2e: one-shot solves through the C ABI from host arrays (create, upload, scaling,
-    solve, download)."""
+    Also all of them as one batch (one launch, one CTA per LP).  e2e: one-shot solves
+    through the C ABI from host arrays (create, upload, scaling, solve, download)."""
     import numpy as np
     import torch
 
@@ -577,6 +577,22 @@ def run_tiny(args):
     single = res["single_cta"]
     total_iters = sum(r["iters"] for r in single)
     total_secs = sum(r["secs"] for r in single)
+    # all of them as one batch: one launch, one CTA per LP
+    solvers = [hpr.Solver(lp, max_iter=args.max_iter) for lp in lps]
+    with hpr.Batch(solvers, stream.cuda_stream) as b:
+        for _ in range(args.warmup):
+            b.solve(args.tol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, bres = b.solve(args.tol)
+        torch.cuda.synchronize()
+        batch_secs = time.perf_counter() - t0
+        bst = b.stats()
+    for s_ in solvers:
+        s_.close()
+    batched = {"lps": len(lps), "seconds": batch_secs, "lp_per_s": len(lps) / batch_secs,
+               "iters_per_s_summed": sum(int(r["info"]["iters"]) for r in bres) / batch_secs,
+               "launches": bst["fused_launches"], "all_ok": all(r["status"] == 0 for r in bres)}
     # end to end from host arrays
     h2d = sum((lp.A1.indptr.size + lp.A2.indptr.size) * 8 + lp.nnz * 12 + lp.m * 8 + lp.n * 24 for lp in lps)
     d2h = sum((2 * lp.n + lp.m) * 8 for lp in lps)
@@ -607,6 +623,7 @@ def run_tiny(args):
                    "count": len(lps), "tol": args.tol,
                    "l2": "working set far below L2 (latency-bound; no flush)"},
         "single_cta": summary(single), "multi_cta": summary(res["multi_cta"]),
+        "batched_single_cta": batched,
         "gpu_launches": int(sum(r["launches"] for r in single)) * args.steps,
         "e2e": {"value": e2e_iters / e2e_secs, "unit": "iter/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_secs},
@@ -639,7 +656,7 @@ def main():
                          "(1M nodes at scale 1), or a batch of uneven planted LPs solved in one "
                          "batched run (m log-uniform in [500, 50000 * scale])")
     ap.add_argument("--count", type=int, default=None,
-                    help="LPs in the batch workload (default 512) or the tiny workload (default 10)")
+                    help="LPs in the batch workload (default 512) or the tiny workload (default 100)")
     ap.add_argument("--qap-n", dest="qap_n", type=int, default=30,
                     help="QAP workload: N (N^4 + N^2 variables)")
     ap.add_argument("--sell-steps", dest="sell_steps", type=int, default=0,
@@ -657,7 +674,7 @@ def main():
                     help="use this lambda instead of the power method (short profiling runs)")
     args = ap.parse_args()
     if args.count is None:
-        args.count = 10 if args.workload == "tiny" else 512
+        args.count = 100 if args.workload == "tiny" else 512
     if args.workload == "tiny" and args.impl == "ours":
         run_tiny(args)
     elif args.impl == "reference" and args.workload == "batch":

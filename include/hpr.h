@@ -272,6 +272,9 @@ int hpr_get_layout(const hpr_ctx *ctx, int64_t *sell_steps, double *unit_cost, i
  *                default for small phases (no layout options, no autotune) get the
  *                default layout (40, 64) instead, for good (hpr_get_layout shows it).
  *   cuda_stream  the batch's stream (NULL: a stream of its own).
+ * When every context would take the persistent single-CTA path on its own (see
+ * hpr_options.persistent), the batch runs them as one launch with one CTA per LP, each
+ * result equal to the context's own single-CTA solve (hpr_batch_stats: 0 periods, 1 launch).
  * hpr_batch_solve returns HPR_OK when every context converged, else the status of a
  * context that did not (HPR_MAX_ITER / HPR_TIME_LIMIT), or an error code; detail in
  * hpr_last_error(NULL) or of the context. */

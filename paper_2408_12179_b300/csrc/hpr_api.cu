@@ -166,6 +166,7 @@ struct hpr_ctx {
     hpr_check_record *small_recs = nullptr;   // persistent path: its check records and results
     double *small_out = nullptr;
     int small_cap = 0;
+    hprsmall::SmallArgs *small_args = nullptr; // persistent path: device copy of its arguments
     bool batched = false;         // owned by a batch: solved only through hpr_batch_solve
     std::vector<hpr_check_record> checks;
     std::string err;
@@ -376,7 +377,7 @@ void free_all(hpr_ctx *c)
                    c->l_s, c->u_s, c->l_o, c->u_o, c->x, c->x0, c->xhat, c->xbar,
                    c->zbar, c->dx, c->y, c->y0, c->ybar, c->dy, c->xo, c->yo, c->zo,
                    c->partials, c->scal, c->ctl, c->pctl, c->trace, c->policy_wb, c->policy_w32,
-                   c->policy_x, c->policy_q, c->small_recs, c->small_out};
+                   c->policy_x, c->policy_q, c->small_recs, c->small_out, c->small_args};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->scal_h) cudaFreeHost(c->scal_h);
@@ -1728,7 +1729,10 @@ const char *small_unfit(const hpr_ctx *ctx, bool forced)
     return nullptr;
 }
 
-int solve_small(hpr_ctx *ctx, double tol)
+// the launch arguments of a single-CTA solve of ctx with tolerance tol, and its dynamic
+// shared memory; resets the context's solve state (buffers for the check records and the
+// results are allocated on first use and kept)
+int small_prepare(hpr_ctx *ctx, double tol, hprsmall::SmallArgs &A, size_t *smem)
 {
     using namespace hprsmall;
     const hpr_options &o = ctx->opt;
@@ -1752,15 +1756,13 @@ int solve_small(hpr_ctx *ctx, double tol)
         ctx->small_cap = cap;
     }
     if (!ctx->small_out) DALLOC(ctx->small_out, SO_LEN);
-    hpr_check_record *recs = ctx->small_recs;
-    double *out = ctx->small_out;
     auto mat_of = [](const SellDev &D) {
         SmallMat M{};
         M.nslices = D.nslices; M.entries = D.entries;
         M.srow = D.srow; M.sptr = D.sptr; M.col = D.col; M.slg = D.slg; M.val = D.val;
         return M;
     };
-    SmallArgs A{};
+    A = SmallArgs{};
     A.m = (int)m; A.n = (int)n;
     A.A = mat_of(ctx->SA); A.T = mat_of(ctx->ST);
     A.ineq = ctx->ineq;
@@ -1775,40 +1777,65 @@ int solve_small(hpr_ctx *ctx, double tol)
     A.mat_smem = small_smem_bytes((int)m, (int)n, A.A, A.T, true) <= SMALL_SMEM_MAX ? 1 : 0;
     A.perm_r = ctx->perm_r;
     A.xbar_out = ctx->xbar; A.ybar_out = ctx->ybar; A.zbar_out = ctx->zbar;
-    A.recs = recs; A.rec_cap = cap; A.out = out;
-    const size_t smem = small_smem_bytes((int)m, (int)n, A.A, A.T, A.mat_smem != 0);
-    int st = HPR_OK;
-    cudaError_t e = cudaFuncSetAttribute(k_solve_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) {
-        k_solve_small<<<1, NT, smem, s>>>(A);
-        e = cudaGetLastError();
-    }
+    A.recs = ctx->small_recs; A.rec_cap = cap; A.out = ctx->small_out;
+    *smem = small_smem_bytes((int)m, (int)n, A.A, A.T, A.mat_smem != 0);
+    return HPR_OK;
+}
+
+// a finished single-CTA solve into the context's state: its results, check records and
+// the back-map to the original LP
+int small_collect(hpr_ctx *ctx)
+{
+    using namespace hprsmall;
+    SolveState &S = ctx->ss;
     double h[SO_LEN];
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) st = fail_cuda(ctx, e, "solve_small", __LINE__);
-    if (st == HPR_OK) {
-        ctx->launches = 1;
-        const int64_t nrec = std::min<int64_t>((int64_t)h[SO_NREC], cap);
-        ctx->checks.resize((size_t)nrec);
-        if (nrec && cudaMemcpy(ctx->checks.data(), recs, sizeof(hpr_check_record) * nrec, cudaMemcpyDeviceToHost) != cudaSuccess)
-            st = fail_arg(ctx, HPR_ERR_CUDA, "solve_small: check records");
-        ctx->lambda = h[SO_LAMBDA];
-        ctx->power_iters = (int64_t)h[SO_POWER_ITERS];
-        ctx->power_time = h[SO_POWER_S];
-        S.lambda = h[SO_LAMBDA];
-        S.k = (int64_t)h[SO_ITERS]; S.r = (int64_t)h[SO_RESTARTS]; S.sigma = h[SO_SIGMA];
-        S.status = (int)h[SO_STATUS];
-        S.last_pobj = h[SO_POBJ]; S.last_dobj = h[SO_DOBJ]; S.last_ep = h[SO_ERRP]; S.last_ed = h[SO_ERRD];
-        S.last_gap = h[SO_GAP]; S.last_kkt = h[SO_KKT];
-        S.time_1e4 = h[SO_T1E4] >= 0.0 ? h[SO_T1E4] : -1.0;
-        S.iters_1e4 = (int64_t)h[SO_I1E4];
-        S.done = true;
-        if (S.status == HPR_ERR_NUMERIC)
-            st = fail_arg(ctx, HPR_ERR_NUMERIC, "non-finite residual at iteration " + std::to_string(S.k - 1));
-    }
-    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(h, ctx->small_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "solve_small", __LINE__);
+    ctx->launches = 1;
+    const int64_t nrec = std::min<int64_t>((int64_t)h[SO_NREC], ctx->small_cap);
+    ctx->checks.resize((size_t)nrec);
+    if (nrec && cudaMemcpy(ctx->checks.data(), ctx->small_recs, sizeof(hpr_check_record) * nrec,
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail_arg(ctx, HPR_ERR_CUDA, "solve_small: check records");
+    ctx->lambda = h[SO_LAMBDA];
+    ctx->power_iters = (int64_t)h[SO_POWER_ITERS];
+    ctx->power_time = h[SO_POWER_S];
+    S.lambda = h[SO_LAMBDA];
+    S.k = (int64_t)h[SO_ITERS]; S.r = (int64_t)h[SO_RESTARTS]; S.sigma = h[SO_SIGMA];
+    S.status = (int)h[SO_STATUS];
+    S.last_pobj = h[SO_POBJ]; S.last_dobj = h[SO_DOBJ]; S.last_ep = h[SO_ERRP]; S.last_ed = h[SO_ERRD];
+    S.last_gap = h[SO_GAP]; S.last_kkt = h[SO_KKT];
+    S.time_1e4 = h[SO_T1E4] >= 0.0 ? h[SO_T1E4] : -1.0;
+    S.iters_1e4 = (int64_t)h[SO_I1E4];
+    S.done = true;
+    if (S.status == HPR_ERR_NUMERIC)
+        return fail_arg(ctx, HPR_ERR_NUMERIC, "non-finite residual at iteration " + std::to_string(S.k - 1));
     return solve_finish(ctx);
+}
+
+// launches k_solve_small over `count` argument blocks (one CTA each) on stream s
+cudaError_t small_launch(const hprsmall::SmallArgs *args_dev, int count, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(hprsmall::k_solve_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    hprsmall::k_solve_small<<<count, hprsmall::NT, smem, s>>>(args_dev);
+    return cudaGetLastError();
+}
+
+int solve_small(hpr_ctx *ctx, double tol)
+{
+    using namespace hprsmall;
+    SmallArgs A;
+    size_t smem = 0;
+    int st = small_prepare(ctx, tol, A, &smem);
+    if (st) return st;
+    if (!ctx->small_args) DALLOC(ctx->small_args, 1);
+    cudaError_t e = cudaMemcpyAsync(ctx->small_args, &A, sizeof A, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = small_launch(ctx->small_args, 1, smem, ctx->stream);
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "solve_small", __LINE__);
+    return small_collect(ctx);
 }
 
 }  // namespace
@@ -2046,6 +2073,8 @@ struct hpr_batch {
     int64_t power_threads = 8;
     double solve_time = 0.0;
     int64_t periods = 0, fused_launches = 0;
+    hprsmall::SmallArgs *small_args = nullptr;   // single-CTA launch: one argument block per LP
+    size_t small_cap = 0;
 };
 
 namespace {
@@ -2056,7 +2085,7 @@ void batch_free(hpr_batch *b)
     b->graphs.clear();
     void *dev[] = {b->tasksT, b->tasksA, b->sellT64, b->sellA64, b->sellT32, b->sellA32, b->ex, b->ey,
                    b->ex32, b->ey32, b->exc, b->eyc, b->exc32, b->eyc32, b->edual, b->eprim, b->red,
-                   b->ctl_all, b->scal_all};
+                   b->ctl_all, b->scal_all, b->small_args};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (b->ctl_all_h) cudaFreeHost(b->ctl_all_h);
@@ -2066,6 +2095,60 @@ void batch_free(hpr_batch *b)
         c->batched = false;
     }
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+// whether every context of the batch would take the persistent single-CTA path on its own
+bool batch_all_small(const hpr_batch *b)
+{
+    for (const hpr_ctx *c : b->ctxs)
+        if (c->opt.persistent == 0 || small_unfit(c, c->opt.persistent == 2)) return false;
+    return true;
+}
+
+// A batch of LPs that all take the persistent single-CTA path: one launch of k_solve_small
+// with one CTA per LP (each LP on an SM of its own, the LPs independent of one another), then
+// each context's results read back as after its own solve.
+int batch_small(hpr_batch *b, double tol)
+{
+    using namespace hprsmall;
+    std::vector<hpr_ctx *> &cs = b->ctxs;
+    const double t0 = now_s();
+    std::vector<SmallArgs> args(cs.size());
+    size_t smem = 0;
+    for (size_t i = 0; i < cs.size(); ++i) {
+        size_t si = 0;
+        const int st = small_prepare(cs[i], tol, args[i], &si);
+        if (st) return st;
+        smem = std::max(smem, si);
+    }
+    if (b->small_cap < cs.size()) {
+        if (b->small_args) cudaFree(b->small_args);
+        b->small_args = nullptr;
+        b->small_cap = 0;
+        if (cudaMalloc((void **)&b->small_args, sizeof(SmallArgs) * cs.size()) != cudaSuccess) {
+            g_static_err = "hpr_batch_solve: single-CTA arguments could not be allocated";
+            return HPR_ERR_NOMEM;
+        }
+        b->small_cap = cs.size();
+    }
+    cudaError_t e = cudaMemcpyAsync(b->small_args, args.data(), sizeof(SmallArgs) * cs.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = small_launch(b->small_args, (int)cs.size(), smem, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        g_static_err = "hpr_batch_solve: single-CTA launch failed";
+        return HPR_ERR_CUDA;
+    }
+    int status = HPR_OK;
+    for (hpr_ctx *c : cs) {
+        const int st = small_collect(c);
+        if (st < 0) return st;
+        if (st != HPR_OK && status == HPR_OK) status = st;
+    }
+    b->periods = 0;
+    b->fused_launches = 1;
+    b->solve_time = now_s() - t0;
+    return status;
 }
 
 template <class T>
@@ -2244,9 +2327,10 @@ int hpr_batch_create(hpr_batch **out, int64_t count, hpr_ctx *const *ctxs, void 
             sx += phase_bytes_x(c);
             sy += phase_bytes_y(c);
         }
-        for (hpr_ctx *c : cs)
-            if (relayout_for_throughput(c, sy >= SMALL_PHASE_BYTES, sx >= SMALL_PHASE_BYTES) != HPR_OK)
-                return fail(HPR_ERR_CUDA, "hpr_batch_create: relayout for throughput failed");
+        if (!batch_all_small(b))     // (a batch of single-CTA solves keeps the short slices)
+            for (hpr_ctx *c : cs)
+                if (relayout_for_throughput(c, sy >= SMALL_PHASE_BYTES, sx >= SMALL_PHASE_BYTES) != HPR_OK)
+                    return fail(HPR_ERR_CUDA, "hpr_batch_create: relayout for throughput failed");
     }
     std::vector<MultiTask> tT = fused_tasks(cs, true), tA = fused_tasks(cs, false);
     int st = HPR_OK;
@@ -2281,6 +2365,7 @@ int hpr_batch_solve(hpr_batch *b, double tol)
             return HPR_ERR_ARG;
         }
     }
+    if (batch_all_small(b)) return batch_small(b, tol);
     const double t0 = now_s();
     b->periods = 0;
     b->fused_launches = 0;

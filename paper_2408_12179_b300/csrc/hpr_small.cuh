@@ -269,8 +269,11 @@ __device__ SmallMat stage_mat(const SmallMat &M, double *&dv, int *&di, unsigned
     return S;
 }
 
-__global__ void __launch_bounds__(NT) k_solve_small(SmallArgs P)
+// one LP per CTA: block b solves the LP of args[b] (a solo solve launches one block; a batch
+// of LPs that all fit launches one block per LP, each on an SM of its own)
+__global__ void __launch_bounds__(NT) k_solve_small(const SmallArgs *__restrict__ args)
 {
+    SmallArgs P = args[blockIdx.x];
     extern __shared__ double sh[];
     const int n = P.n, m = P.m, tid = threadIdx.x;
     double *x = sh, *x0 = x + n, *xh = x0 + n, *xb = xh + n, *zb = xb + n, *dx = zb + n;

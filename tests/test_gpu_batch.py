@@ -123,3 +123,25 @@ def test_large_batch_lays_out_small_contexts_for_throughput():
     finally:
         for s in solvers:
             s.close()
+
+
+def test_batch_of_single_cta_solves():
+    """A batch whose LPs all take the persistent single-CTA path runs as one launch, one CTA
+    per LP; each result equals that LP's own single-CTA solve bit for bit."""
+    lps = [lpgen.planted_tiny(seed) for seed in range(12)] + [lpgen.planted_tiny(3, m1=0, m2=90, n=170)]
+    solvers = [hpr.Solver(lp) for lp in lps]
+    try:
+        with hpr.Batch(solvers) as b:
+            status, res = b.solve(1e-8)
+            st = b.stats()
+        assert status == hpr.HPR_OK and st["fused_launches"] == 1 and st["periods"] == 0
+        for lp, r in zip(lps, res):
+            with hpr.Solver(lp, persistent=2) as s:
+                solo = s.solve(1e-8)
+            assert r["info"]["iters"] == solo["info"]["iters"], lp.name
+            assert r["info"]["lambda"] == solo["info"]["lambda"], lp.name
+            for key in ("x", "y", "z"):
+                assert np.array_equal(r[key], solo[key]), (lp.name, key)
+    finally:
+        for s in solvers:
+            s.close()
