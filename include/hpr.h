@@ -252,6 +252,26 @@ int hpr_power_noalloc(int64_t m, int64_t n, const int32_t *A_row_ptr, const int3
  * be NULL.  Returns HPR_OK or HPR_ERR_ARG (ctx NULL). */
 int hpr_get_layout(const hpr_ctx *ctx, int64_t *sell_steps, double *unit_cost, int64_t *units);
 
+/* Host only (no device work, no context; for tests and tools): the sliced-ELL layout that
+ * hpr_create builds for the rows of the CSR matrix B, with B's own column numbering.  Rows
+ * are taken in order of decreasing length (stable) in groups of 32; a group gives each row
+ * L = 2^slg lanes, the fewest (L <= 32) that keep its longest row within steps_max steps,
+ * and is stored as L slices of 32 / L rows, column-major: entry e of the q-th row of a slice
+ * sits at sptr[s] + (e / L) * 32 + q * L + e % L.  Work units (one warp each) are a group
+ * whole, or each of its slices when the group's cost (steps + 2 + log2 L + the epilogue's
+ * share 8 * rows / 32, summed over its slices) exceeds unit_cost.
+ *   steps_max in [1, 4096], unit_cost > 0: the layout parameters (hpr_options.sell_steps_*,
+ *   unit_cost_*).  Sizes go to *nslices, *entries (stored entries, padding included) and
+ *   *units (any may be NULL).  Each array may be NULL, else it must hold: row_order rows
+ *   (row_order[new] = old), srow and sptr nslices + 1 (first row, first entry of slice s),
+ *   slg nslices, col and src entries (src: the CSR position of each stored entry, -1 for
+ *   padding, whose col is 0), wstart units + 1 (first slice of each unit).  Call once with
+ *   NULL arrays for the sizes.  Returns HPR_OK, or HPR_ERR_ARG (bad matrix or parameters;
+ *   detail in hpr_last_error(NULL)). */
+int hpr_layout_plan(const hpr_csr *B, int64_t steps_max, double unit_cost, int64_t *nslices, int64_t *entries,
+                    int64_t *units, int32_t *row_order, int32_t *srow, int32_t *sptr, uint8_t *slg, int32_t *col,
+                    int32_t *src, int32_t *wstart);
+
 /* ---- Batched solve (no counterpart in the paper: many independent LPs in lock step).
  * A batch takes `count` contexts made by hpr_create (their LPs may differ in size and
  * structure) and solves them together: each check period's normal iterations of all

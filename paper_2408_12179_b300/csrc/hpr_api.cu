@@ -1912,6 +1912,56 @@ int hpr_get_layout(const hpr_ctx *ctx, int64_t *sell_steps, double *unit_cost, i
     return HPR_OK;
 }
 
+int hpr_layout_plan(const hpr_csr *B, int64_t steps_max, double unit_cost, int64_t *nslices, int64_t *entries,
+                    int64_t *units, int32_t *row_order, int32_t *srow, int32_t *sptr, uint8_t *slg, int32_t *col,
+                    int32_t *src, int32_t *wstart)
+{
+    if (!B || B->rows < 0 || B->cols < 0 || B->nnz < 0 || B->rows >= (int64_t)INT32_MAX ||
+        B->cols >= (int64_t)INT32_MAX || B->nnz >= (int64_t)INT32_MAX || !B->row_ptr ||
+        (B->nnz > 0 && !B->col_idx) || !(steps_max >= 1 && steps_max <= 4096) || !(unit_cost > 0.0)) {
+        g_static_err = "hpr_layout_plan: bad matrix or parameters";
+        return HPR_ERR_ARG;
+    }
+    const int rows = (int)B->rows;
+    if (B->row_ptr[0] != 0 || B->row_ptr[rows] != B->nnz) {
+        g_static_err = "hpr_layout_plan: row_ptr[0] != 0 or row_ptr[rows] != nnz";
+        return HPR_ERR_ARG;
+    }
+    std::vector<int> rp((size_t)rows + 1), ci((size_t)std::max<int64_t>(B->nnz, 1), 0), icol((size_t)B->cols);
+    for (int i = 0; i <= rows; ++i) {
+        rp[(size_t)i] = (int)B->row_ptr[i];
+        if (i > 0 && rp[(size_t)i] < rp[(size_t)i - 1]) {
+            g_static_err = "hpr_layout_plan: row_ptr decreases";
+            return HPR_ERR_ARG;
+        }
+    }
+    for (int64_t p = 0; p < B->nnz; ++p) {
+        if (B->col_idx[p] < 0 || B->col_idx[p] >= B->cols) {
+            g_static_err = "hpr_layout_plan: column index out of range";
+            return HPR_ERR_ARG;
+        }
+        ci[(size_t)p] = B->col_idx[p];
+    }
+    for (int64_t j = 0; j < B->cols; ++j) icol[(size_t)j] = (int)j;
+    const std::vector<int> perm = order_by_length(rp, rows);
+    const SellHost H = build_sell(rp, ci, rows, perm, icol, (int)steps_max, unit_cost);
+    const int64_t nu = (int64_t)H.wstart.size() - 1;
+    if (nslices) *nslices = H.nslices;
+    if (entries) *entries = (int64_t)H.col.size();
+    if (units) *units = nu;
+    auto put = [](int32_t *dst, const std::vector<int> &v) {
+        if (dst && !v.empty()) memcpy(dst, v.data(), sizeof(int32_t) * v.size());
+    };
+    put(row_order, perm);
+    put(srow, H.srow);
+    put(sptr, H.sptr);
+    put(col, H.col);
+    put(src, H.src);
+    put(wstart, H.wstart);
+    if (slg && !H.slg.empty()) memcpy(slg, H.slg.data(), H.slg.size());
+    return HPR_OK;
+}
+
 int hpr_get_checks(const hpr_ctx *ctx, hpr_check_record *out, int64_t cap, int64_t *count)
 {
     if (!ctx) return HPR_ERR_ARG;

@@ -98,6 +98,9 @@ SIGNATURES = {
                                          ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, _D, _I64]),
     "hpr_get_layout": (ctypes.c_int, [ctypes.c_void_p, _I64, _D, _I64]),
+    "hpr_layout_plan": (ctypes.c_int, [ctypes.POINTER(hpr_csr), ctypes.c_int64, ctypes.c_double, _I64, _I64,
+                                       _I64, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_uint8), _I32, _I32,
+                                       _I32]),
     "hpr_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "hpr_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
@@ -172,6 +175,26 @@ def _block(M, n):
     ci = np.ascontiguousarray(M.indices, dtype=np.int32)
     v = np.ascontiguousarray(M.data, dtype=np.float64)
     return hpr_csr(M.shape[0], M.shape[1], v.size, _ptr(rp, _I64), _ptr(ci, _I32), _ptr(v)), (rp, ci, v)
+
+
+def layout_plan(M, steps_max=40, unit_cost=64.0):
+    """The sliced-ELL layout hpr_create builds for the rows of the SciPy CSR matrix M (host
+    only, no GPU): dict of numpy arrays row_order, srow, sptr, slg, col, src, wstart."""
+    lib = load()
+    B, keep = _block(M, M.shape[1])
+    ns, ne, nu = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.hpr_layout_plan(ctypes.byref(B), int(steps_max), float(unit_cost), ctypes.byref(ns), ctypes.byref(ne),
+                               ctypes.byref(nu), None, None, None, None, None, None, None))
+    out = dict(row_order=np.zeros(M.shape[0], np.int32), srow=np.zeros(ns.value + 1, np.int32),
+               sptr=np.zeros(ns.value + 1, np.int32), slg=np.zeros(ns.value, np.uint8),
+               col=np.zeros(ne.value, np.int32), src=np.zeros(ne.value, np.int32),
+               wstart=np.zeros(nu.value + 1, np.int32))
+    _check(lib.hpr_layout_plan(ctypes.byref(B), int(steps_max), float(unit_cost), None, None, None,
+                               _ptr(out["row_order"], _I32), _ptr(out["srow"], _I32), _ptr(out["sptr"], _I32),
+                               _ptr(out["slg"], ctypes.POINTER(ctypes.c_uint8)), _ptr(out["col"], _I32),
+                               _ptr(out["src"], _I32), _ptr(out["wstart"], _I32)))
+    del keep
+    return out
 
 
 def _check(code, ctx=None):
