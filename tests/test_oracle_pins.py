@@ -343,6 +343,44 @@ def _M_norm(A, sigma, lam, dy, dx):
     return math.sqrt(max(q, 0.0))
 
 
+def test_merit_is_the_M_norm_of_its_definition(orc):
+    """The merit that drives the restart criteria (Section 3.1), R~ = ||w - w_hat||_M =
+    2 ||w - w_bar||_M, with M built as a dense matrix from its block definition (eq. def:M,
+    unsimplified: sigma A A^* + sigma T1 with T1 = lambda I - A A^*, a zero z block, A and
+    A^* off the diagonal, I / sigma), equals the oracle's recorded value at every check of
+    the traced iterations: the R~_{r,0} evaluations and the periodic checks, across restarts
+    and sigma changes.  The z part of w - w_bar is random: the zero block must ignore it."""
+    lp = lpgen.planted_tiny(0)
+    s = _scaled(orc, lp)
+    A = s["A"].toarray()
+    m, n = lp.m, lp.n
+    N = 1200
+    r = orc.solve(lp, max_iter=N, trace_iters=N)
+    lam = r["info"]["lambda"]
+    tr = r["trace"]
+    rng = np.random.default_rng(5)
+    seen_kinds, sigmas = set(), set()
+    for c in r["checks"]:
+        k = int(c["k"])
+        if k >= min(N, int(r["info"]["iters"]) - 1):    # (the terminating iteration is not traced)
+            continue
+        sigma = c["sigma"]
+        T1 = lam * np.eye(m) - A @ A.T
+        M = np.zeros((m + 2 * n, m + 2 * n))
+        M[:m, :m] = sigma * (A @ A.T) + sigma * T1
+        M[:m, m + n:] = A
+        M[m + n:, :m] = A.T
+        M[m + n:, m + n:] = np.eye(n) / sigma
+        d = np.concatenate([_prev(tr, "y", k, m) - tr["ybar"][k], rng.standard_normal(n),
+                            _prev(tr, "x", k, n) - tr["xbar"][k]])
+        q = d @ M @ d
+        assert q >= -1e-12 * (d @ d)
+        assert c["Rt"] == pytest.approx(2.0 * math.sqrt(max(q, 0.0)), rel=1e-8, abs=1e-14), (k, c["kind"])
+        seen_kinds.add(int(c["kind"]))
+        sigmas.add(sigma)
+    assert {1, 2} <= seen_kinds and len(sigmas) >= 2     # periodic checks, R~_{r,0}, several sigmas
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_prop_2_9_and_theorem_3_7_bounds(orc, seed):
     """Proposition 2.9: ||w^k - w_hat^{k+1}||_M <= 2 ||w^0 - w*||_M / (k+1) and Theorem 3.7:
