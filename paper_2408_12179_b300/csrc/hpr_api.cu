@@ -283,8 +283,10 @@ SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int 
     auto len = [&](int i) { return rp[(size_t)perm[(size_t)i] + 1] - rp[(size_t)perm[(size_t)i]]; };
     std::vector<double> scost;       // cost of each slice (epilogue share included)
     std::vector<int> gfirst;         // first slice of each group
+    // pass 1: the slices (rows, lanes, steps) and where each one's entries start
     h.srow.push_back(0);
     h.sptr.push_back(0);
+    size_t total = 0;
     for (int g0 = 0; g0 < rows; g0 += 32) {
         const int g1 = std::min(rows, g0 + 32);
         const int lmax = len(g0);
@@ -295,9 +297,24 @@ SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int 
         for (int r = g0; r < g1; r += per) {
             const int r1 = std::min(g1, r + per);
             const int steps = (len(r) + L - 1) / L;
-            const size_t base = h.col.size();
-            h.col.resize(base + (size_t)32 * steps, 0);
-            h.src.resize(base + (size_t)32 * steps, -1);
+            total += (size_t)32 * steps;
+            h.slg.push_back((unsigned char)lg);
+            h.srow.push_back(r1);
+            h.sptr.push_back((int)total);
+            h.nslices++;
+            scost.push_back((double)steps + 2.0 + lg + 8.0 * (r1 - r) / 32.0);
+        }
+    }
+    gfirst.push_back(h.nslices);
+    // pass 2: every slice's entries into its own range (padding: column 0, no source), on
+    // up to 16 host threads over contiguous runs of slices of about equal size
+    h.col.assign(total, 0);
+    h.src.assign(total, -1);
+    auto fill = [&](int s0, int s1) {
+        for (int sl = s0; sl < s1; ++sl) {
+            const int lg = h.slg[(size_t)sl], L = 1 << lg;
+            const int r = h.srow[(size_t)sl], r1 = h.srow[(size_t)sl + 1];
+            const size_t base = (size_t)h.sptr[(size_t)sl];
             for (int q = 0; q < r1 - r; ++q) {
                 const int orow = perm[(size_t)(r + q)];
                 for (int e = 0, p = rp[(size_t)orow]; p < rp[(size_t)orow + 1]; ++p, ++e) {
@@ -306,14 +323,25 @@ SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int 
                     h.src[at] = p;
                 }
             }
-            h.slg.push_back((unsigned char)lg);
-            h.srow.push_back(r1);
-            h.sptr.push_back((int)h.col.size());
-            h.nslices++;
-            scost.push_back((double)steps + 2.0 + lg + 8.0 * (r1 - r) / 32.0);
         }
+    };
+    const int nthr = total < ((size_t)1 << 20)
+                         ? 1
+                         : (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (nthr == 1) {
+        fill(0, h.nslices);
+    } else {
+        std::vector<std::thread> pool;
+        int s0 = 0;
+        for (int t = 0; t < nthr && s0 < h.nslices; ++t) {
+            const size_t goal = total * (size_t)(t + 1) / (size_t)nthr;
+            int s1 = s0;
+            while (s1 < h.nslices && (t == nthr - 1 || (size_t)h.sptr[(size_t)s1] < goal)) ++s1;
+            pool.emplace_back(fill, s0, s1);
+            s0 = s1;
+        }
+        for (auto &th : pool) th.join();
     }
-    gfirst.push_back(h.nslices);
     // work units: a light group whole, a heavy group by slice
     h.wstart.clear();
     for (size_t g = 0; g + 1 < gfirst.size(); ++g) {
