@@ -46,3 +46,18 @@ def test_tiny_planted_point_is_feasible_and_complementary(seed):
     assert np.allclose(slack * y[lp.m1:], 0.0, atol=1e-12)   # complementary slackness
     assert np.all((z <= 1e-15) | (np.abs(x - lp.l) < 1e-12))
     assert np.all((z >= -1e-15) | (np.abs(x - lp.u) < 1e-12))
+
+
+def test_batch_family_ranges():
+    """The batched family: m in [m_lo, m_hi] (even), n = 2.5 m, density in [0.1%, 1%] up to the
+    stochastic rounding of the column counts, planted optimum feasible; reproducible."""
+    lps = lpgen.batch_family(0, 24, 500, 5000)
+    again = lpgen.batch_family(0, 24, 500, 5000)
+    for lp, lp2 in zip(lps, again):
+        assert 500 <= lp.m <= 5002 and lp.m % 2 == 0 and lp.n == int(round(2.5 * lp.m))
+        dens = lp.nnz / (lp.m * lp.n)
+        assert 0.8e-3 <= dens <= 1.2e-2, (lp.name, dens)
+        assert lp.nnz == lp2.nnz and np.array_equal(lp.c, lp2.c)
+        assert np.allclose(lp.A1 @ lp.x_star, lp.b1) and np.all(lp.A2 @ lp.x_star >= lp.b2 - 1e-9)
+    ms = np.log([lp.m for lp in lps])
+    assert ms.max() - ms.min() > 1.0             # spread over the log-uniform range
