@@ -73,7 +73,7 @@ bool batch_all_small(const hpr_batch *b)
 }
 
 // A batch of LPs that all take the persistent single-CTA path: one launch of k_solve_small
-// with one CTA per LP (each LP on an SM of its own, the LPs independent of one another), then
+// with one CTA per LP (at most two per SM, the LPs independent of one another), then
 // each context's results read back as after its own solve.
 int batch_small(hpr_batch *b, double tol)
 {

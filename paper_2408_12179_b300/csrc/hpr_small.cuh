@@ -270,7 +270,8 @@ __device__ SmallMat stage_mat(const SmallMat &M, double *&dv, int *&di, unsigned
 }
 
 // one LP per CTA: block b solves the LP of args[b] (a solo solve launches one block; a batch
-// of LPs that all fit launches one block per LP, each on an SM of its own)
+// of LPs that all fit launches one block per LP; 1024 threads a block, so at most two
+// share an SM)
 __global__ void __launch_bounds__(NT) k_solve_small(const SmallArgs *__restrict__ args)
 {
     SmallArgs P = args[blockIdx.x];
