@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = ("time-to-KKT≤1e-8 (s), HPR iters/s, HBM GB/s % of peak; chosen form vs plain FP64")
+L2_BYTES = 126e6   # B300 L2
 BATCH_METRIC = "HPR iterations/s summed over the LPs of the batch workload (LPs solved to tol per second beside it)"
 
 # DRAM bytes per launch from one ncu capture of the medium planted LP (seed 0, full size,
@@ -207,11 +208,15 @@ def config_dict(args, lp):
     else:
         name = (f"medium sparse planted LP (m={lp.m}, m1={lp.m1}, n={lp.n}, nnz={lp.nnz}, "
                 f"Zipf(1.5) column counts, values +-10^U(-3,3), 20% free columns, seed {args.seed})")
+    bx, by = algorithmic_bytes(lp.nnz, lp.n, lp.m, args.precision)
+    l2 = ("working set per iteration larger than L2 (no flush)" if bx + by > L2_BYTES else
+          f"working set per iteration ({(bx + by) / 1e6:.0f} MB) fits in L2 (no flush: every iteration "
+          f"of a solve re-reads the same data)")
     return {"workload": name,
             "scale": args.scale, "tol": args.tol,
             "precision": "fp64" if args.precision == 0 else "fp32 form, fp64 below kkt 1e-5",
             "variant": args.variant,
-            "l2": "working set per iteration larger than L2 (no flush)"}
+            "l2": l2}
 
 
 def run_reference(args):
@@ -330,6 +335,9 @@ def run_batch(args):
     if rank != 0:
         return
     nnz = sum(lp.nnz for lp in lps)
+    bsum = sum(sum(algorithmic_bytes(lp.nnz, lp.n, lp.m, args.precision)) for lp in lps)
+    batch_l2 = (f"all LPs' working sets together ({bsum / 1e6:.0f} MB a fused iteration) "
+                + ("larger than L2 (no flush)" if bsum > L2_BYTES else "fit in L2 (no flush)"))
     line = {
         "metric": BATCH_METRIC, "value": iters / secs, "unit": "iter/s", "lp_per_s": len(conv) / secs,
         "n_gpus": 1, "steps": 1, "warmup": args.warmup,
@@ -341,6 +349,7 @@ def run_batch(args):
                    "tol": args.tol, "max_iter": args.max_iter, "variant": args.variant,
                    "autotune": ({str(k): v for k, v in sorted(tuned.items())} if tuned else None),
                    "layout": layout_opts(args) or "library default",
+                   "l2": batch_l2,
                    "create_s": create_secs},
         "batch_status": hpr.hpr_status_str(int(status)), "converged": len(conv), "count": len(lps),
         "time_to_all_s": secs, "iters_summed": iters, "iters_per_s_summed": iters / secs,
