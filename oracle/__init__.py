@@ -11,8 +11,10 @@ Section 3.1, Algorithm 3 and the termination test of Section 4.1).  ``kkt`` (mod
 original LP, written in numpy.
 
 Parity pins: see the test-suite (``tests/test_oracle_*.py``).  Every function here is
-pinned except the restart/sigma decision sequence, for which the paper prints no trace:
-parity unpinned for that sequence (it is compared only between the two solvers).
+pinned; the restart / sigma decision sequence, for which the paper prints no trace, is
+rebuilt check by check from the rules of Section 3.1 and Algorithm 3
+(``tests/test_oracle_restart.py``, which also plants misreadings of the rules in a copy of
+the C source and checks that the rebuild rejects each one).
 """
 from __future__ import annotations
 
