@@ -223,21 +223,23 @@ int hpr_time_iteration(hpr_ctx *ctx, int64_t reps, double *ms_x, double *ms_y, d
  * themselves -- code that runs under a memory budget or pool owned by someone else
  * (an inference server, a framework's caching allocator) or that must not call
  * cudaMalloc at that point -- and that already hold the LP matrix on the device.
- * Computes the same lambda_1(A A^*) as hpr_power on the given matrix, but allocates
+ * Computes the same lambda_1(A A^*) as hpr_power on the given matrix (the largest
+ * eigenvalue of A A^* by power iteration from a SplitMix64 start vector), but allocates
  * nothing: its per-CTA partial sums, reduced scalars and control block live in one
  * fixed array of 131,456 bytes in device global memory that is part of the library
  * and stays allocated on every device that loaded the library until the process exits.
  *   m, n            rows and columns of A; each in [1, 2^31 - 2] (otherwise HPR_ERR_ARG)
  *   A_*, At_*       DEVICE CSR arrays (32-bit) of A (m rows) and of its transpose
  *                   (n rows), column indices sorted within rows
- *   seed, max_iter, tol   as in hpr_options (power method of Section 4.1)
+ *   seed, max_iter, tol   as in hpr_options (power_max_iter, power_tol)
  *   u (m), s (n)    DEVICE output buffers: the final unit vector u and s = A^T u of
  *                   the last step (both are overwritten during the iteration)
  *   cuda_stream     cudaStream_t to run on (NULL: the legacy default stream)
  *   lambda, iters   HOST outputs (may be NULL)
- * The call synchronises its stream every 16 power steps.  The first call on a device
- * looks up the array's device address with that device current; make that first call
- * before any stream capture.  All calls on a device share the array, so calls that
+ * The call copies a control block to the device and synchronises its stream every 16
+ * power steps, so it must not be made while its stream is being captured into a CUDA
+ * graph.  The first call on a device looks up the array's device address with that
+ * device current.  All calls on a device share the array, so calls that
  * overlap on the GPU (other threads, other streams) race and must be serialised by the
  * caller.  Returns HPR_OK, HPR_ERR_ARG, HPR_ERR_NUMERIC or HPR_ERR_CUDA; the detail is
  * in hpr_last_error(NULL). */
@@ -338,7 +340,10 @@ int hpr_mlp_grad(const float *w, int64_t n, const float *X, const int32_t *act, 
 int hpr_mlp_train(float *w, int64_t n, const float *X, const int32_t *act, const float *y, int64_t epochs,
                   int64_t batch, double lr, uint64_t seed, double *epoch_loss);
 
-/* Detail of the last error of ctx (a static string when ctx is NULL). */
+/* Detail of the last error of ctx.  With ctx NULL: the detail of the last failing call
+ * made without a context (hpr_create, hpr_power_noalloc, hpr_batch_*, hpr_mlp_*,
+ * hpr_layout_plan) on the calling host thread; it stays valid until that thread's next
+ * such failure. */
 const char *hpr_last_error(const hpr_ctx *ctx);
 
 /* Name of a status code. */

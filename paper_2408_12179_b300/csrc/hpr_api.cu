@@ -180,7 +180,9 @@ struct hpr_ctx {
 
 namespace {
 
-const char *g_static_err = "no context";
+// last error of a context-free call, per host thread (each thread reads only its own
+// messages, which live in thread-local storage of the thread that wrote them)
+thread_local const char *g_static_err = "no context";
 
 int fail_cuda(hpr_ctx *c, cudaError_t e, const char *what, int line)
 {

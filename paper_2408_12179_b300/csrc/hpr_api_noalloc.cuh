@@ -6,8 +6,9 @@
 // ====================================================================== allocation-free power method
 //
 // For callers that must not allocate device memory (they run under a memory budget
-// owned by someone else, inside a capture region, or on a pool whose allocator is not
-// theirs).  The LP is theirs, already on the device; this entry point needs only the
+// owned by someone else, or on a pool whose allocator is not theirs).  The call copies a
+// control block to the device and synchronises its stream every 16 power steps, so it
+// must not be made while its stream is being captured into a CUDA graph.  The LP is theirs, already on the device; this entry point needs only the
 // per-CTA partial sums, a few reduced scalars and the power-method control block, and
 // keeps them in one fixed array in device global memory that is part of the library
 // image.  Every device that loads the library holds that array until the process
@@ -36,11 +37,13 @@ __global__ void __launch_bounds__(TB) k_rows_spmv_norm(int rows, const int *__re
     __shared__ double red[TB / 32];
     if (pc->done) return;
     const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (TB / 32);
+    const int64_t warps = (int64_t)gridDim.x * (TB / 32);
     double p = 0.0;
-    for (int r = blockIdx.x * (TB / 32) + (threadIdx.x >> 5); r < rows; r += warps) {
+    // 64-bit counters: rows and row ends may lie within one stride of 2^31
+    for (int64_t r = (int64_t)blockIdx.x * (TB / 32) + (threadIdx.x >> 5); r < rows; r += warps) {
         double s = 0.0;
-        for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) s = fma(val[k], __ldg(xin + ci[k]), s);
+        for (int64_t k = (int64_t)rp[r] + lane; k < (int64_t)rp[r + 1]; k += 32)
+            s = fma(val[k], __ldg(xin + ci[k]), s);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(TB) k_rows_pow_start(int m, uint64_t seed, dou
 {
     __shared__ double red[TB / 32];
     double p = 0.0;
-    for (int i = blockIdx.x * TB + threadIdx.x; i < m; i += gridDim.x * TB) {
+    for (int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x; i < m; i += (int64_t)gridDim.x * TB) {
         const double v = 2.0 * ((double)(splitmix64_at(seed, (uint64_t)i) >> 11) * 0x1.0p-53) - 1.0;
         u[i] = v;
         p = fma(v, v, p);
@@ -71,6 +74,7 @@ std::mutex g_na_mutex;
 double *g_na_ptr[64] = {nullptr};   // device address of g_noalloc_scratch, per device
 thread_local std::string g_na_err;
 
+// the message stays valid on this thread until its next failing context-free call
 int na_fail(int code, const std::string &msg)
 {
     g_na_err = msg;

@@ -872,7 +872,7 @@ __global__ void k_scale_vec(int m, const double *w, double *u, const PowCtl *pc,
 {
     if (pc && pc->done) return;
     const double inv = inv_ptr ? *inv_ptr : pc->inv;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
         u[i] = w[i] * inv;
 }
 

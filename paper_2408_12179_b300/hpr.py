@@ -283,7 +283,16 @@ def hpr_time_iteration(ctx, reps: int):
 def hpr_power_noalloc(m, n, A_ptrs, At_ptrs, seed, max_iter, tol, u_ptr, s_ptr, stream=None):
     """Allocation-free power method on device CSR arrays given as raw device addresses
     (A_ptrs / At_ptrs = (row_ptr, col_idx, val)); u_ptr (m doubles) and s_ptr (n) are
-    device output buffers.  Returns (lambda, iterations)."""
+    device output buffers.  Returns (lambda, iterations).
+
+    stream: a cudaStream_t handle.  When None and torch is loaded, torch's current CUDA
+    stream is used, so that buffers filled on it are ready before the call reads them;
+    without torch, None is the legacy default stream and the caller orders its own streams."""
+    if stream is None:
+        import sys
+        torch = sys.modules.get("torch")
+        if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+            stream = torch.cuda.current_stream().cuda_stream
     lam = ctypes.c_double()
     it = ctypes.c_int64()
     code = load().hpr_power_noalloc(int(m), int(n), *A_ptrs, *At_ptrs, int(seed), int(max_iter),

@@ -150,3 +150,14 @@ def test_sizes_beyond_32_bit_indices_rejected_before_reading(lib):
                           u4.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None)
     assert code == hpr.HPR_ERR_ARG
     assert "2^31" in hpr.hpr_last_error(None)
+
+
+def test_power_noalloc_rejects_sizes_beyond_its_bound(lib):
+    """hpr_power_noalloc accepts m, n in [1, 2^31 - 2] (its kernels step with 64-bit
+    counters, so no row or entry index wraps below that bound) and refuses anything
+    outside from the sizes alone, before touching the device pointers."""
+    for m, n in ((2 ** 31 - 1, 5), (5, 2 ** 31 - 1), (0, 5), (5, -1)):
+        with pytest.raises(hpr.HprError) as e:
+            hpr.hpr_power_noalloc(m, n, (1, 1, 1), (1, 1, 1), 0, 10, 1e-10, 1, 1)
+        assert e.value.code == hpr.HPR_ERR_ARG
+        assert "2^31 - 2" in hpr.hpr_last_error(None)
