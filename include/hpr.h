@@ -21,6 +21,16 @@
  *     of the last error of a context is in hpr_last_error();
  *   - a context is not thread-safe; separate contexts are independent.  A context
  *     uses the CUDA device that was current when it was created.
+ *
+ * Host-side fault injection, for testing the error paths without faulting a GPU (both
+ * read from the environment by hpr_create; unset or 0: off):
+ *   HPR_FAULT_ALLOC=n      the n-th device or pinned host allocation that the context
+ *                          makes (creation and solves counted together) reports
+ *                          out-of-memory: the call returns HPR_ERR_NOMEM and a context
+ *                          that exists stays valid for hpr_destroy;
+ *   HPR_FAULT_NAN_CHECK=n  the check scalars of the n-th check period of the multi-CTA
+ *                          path are replaced by NaN on the host after read-back: the solve
+ *                          returns HPR_ERR_NUMERIC.
  */
 #ifndef HPR_H
 #define HPR_H

@@ -158,6 +158,10 @@ struct hpr_ctx {
     };
     std::unique_ptr<Relayout> relayout;
     int64_t launches = 0;                           // kernels launched by the current solve
+    // host-side fault injection (environment, read at hpr_create; 0: off): the
+    // fault_alloc-th device or pinned allocation of this context reports out-of-memory, and
+    // the scalars of the fault_nan_check-th check period read back as NaN
+    int64_t fault_alloc = 0, alloc_count = 0, fault_nan_check = 0, check_count = 0;
 
     // results
     bool solved = false;
@@ -212,10 +216,27 @@ int fail_arg(hpr_ctx *c, int code, const std::string &msg)
         if (e_ != cudaSuccess) return fail_cuda(ctx, e_, "kernel launch", __LINE__); \
     } while (0)
 
+// whether this allocation is the one HPR_FAULT_ALLOC asks to fail
+bool fault_now(hpr_ctx *ctx)
+{
+    return ctx && ctx->fault_alloc > 0 && ++ctx->alloc_count == ctx->fault_alloc;
+}
+
+#define CKA(call)                                                                 \
+    do {                                                                          \
+        if (fault_now(ctx))                                                       \
+            return fail_cuda(ctx, cudaErrorMemoryAllocation, #call " (HPR_FAULT_ALLOC)", __LINE__); \
+        CK(call);                                                                 \
+    } while (0)
+
 template <class T>
 int dalloc(hpr_ctx *ctx, T **p, int64_t count)
 {
     size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+    if (fault_now(ctx)) {
+        *p = nullptr;
+        return fail_cuda(ctx, cudaErrorMemoryAllocation, "cudaMalloc (HPR_FAULT_ALLOC)", __LINE__);
+    }
     cudaError_t e = cudaMalloc((void **)p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -657,8 +678,8 @@ int ensure_ctl(hpr_ctx *ctx, int cap)
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
     ctx->ctl_bytes = sizeof(DevCtl) + sizeof(double) * 2 * (size_t)cap;
-    CK(cudaMalloc((void **)&ctx->ctl, ctx->ctl_bytes));
-    CK(cudaMallocHost((void **)&ctx->ctl_h, ctx->ctl_bytes));
+    CKA(cudaMalloc((void **)&ctx->ctl, ctx->ctl_bytes));
+    CKA(cudaMallocHost((void **)&ctx->ctl_h, ctx->ctl_bytes));
     memset(ctx->ctl_h, 0, ctx->ctl_bytes);
     ctx->ctl_cap = cap;
     return HPR_OK;
@@ -1000,8 +1021,8 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     DALLOC(ctx->partials, (int64_t)NQ * ctx->pstride);
     DALLOC(ctx->scal, 2 * NQ);
     DALLOC(ctx->pctl, 1);
-    CK(cudaMallocHost((void **)&ctx->scal_h, sizeof(double) * 2 * NQ));
-    CK(cudaMallocHost((void **)&ctx->pctl_h, sizeof(PowCtl)));
+    CKA(cudaMallocHost((void **)&ctx->scal_h, sizeof(double) * 2 * NQ));
+    CKA(cudaMallocHost((void **)&ctx->pctl_h, sizeof(PowCtl)));
     int st = ensure_ctl(ctx, (int)std::min<int64_t>(ctx->opt.check_every, ctx->opt.max_iter));
     if (st) return st;
 
@@ -1230,6 +1251,11 @@ int hpr_create(hpr_ctx **out, const hpr_csr *A1, const hpr_csr *A2, const double
         delete ctx;
         return code;
     };
+    for (auto &kv : {std::make_pair("HPR_FAULT_ALLOC", &ctx->fault_alloc),
+                     std::make_pair("HPR_FAULT_NAN_CHECK", &ctx->fault_nan_check)}) {
+        const char *v = std::getenv(kv.first);
+        *kv.second = v ? std::max(0LL, std::atoll(v)) : 0;
+    }
     if (opt) ctx->opt = *opt;
     else hpr_default_options(&ctx->opt);
     int st = check_options(ctx, &ctx->opt);

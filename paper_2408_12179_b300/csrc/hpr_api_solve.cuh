@@ -219,6 +219,8 @@ int period_after(hpr_ctx *ctx, double elapsed)
     const bool first_r0 = S.first_r0;
     int st;
 
+    if (ctx->fault_nan_check > 0 && ++ctx->check_count == ctx->fault_nan_check)
+        ctx->scal_h[NQ + Q_RP] = std::nan("");   // HPR_FAULT_NAN_CHECK: a poisoned read-back
     const double *S1 = ctx->scal_h + NQ;
     const double *S0 = (first_r0 && L > 1) ? ctx->scal_h : S1;
     const int64_t kk = S.k + L - 1;           // index of the check iteration

@@ -21,11 +21,20 @@ pytestmark = pytest.mark.gpu
 
 import oracle
 from oracle import kkt as K
+from decisions import compare_decisions
 
 
 def rel(a, b):
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / max(nb, 1e-300)
+
+
+def elem(a, b, floor):
+    """Largest entrywise error |a_i - b_i| / max(|b_i|, floor * ||b||_inf)."""
+    scale = np.maximum(np.abs(b), floor * np.max(np.abs(b), initial=0.0))
+    d = np.abs(a - b)
+    return float(np.max(np.where(scale > 0, d / np.where(scale > 0, scale, 1.0), np.where(d > 0, np.inf, 0.0)),
+                        initial=0.0))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -115,6 +124,7 @@ def test_first_100_iterates(name):
     N = 100
     ref = oracle.solve(lp, max_iter=N, trace_iters=N)
     lam = ref["info"]["lambda"]
+    worst = {}
     with hpr.Solver(lp, max_iter=N, trace_iters=N, lambda_fixed=lam) as s:
         s.solve(1e-8)
         for k in range(N):
@@ -125,34 +135,11 @@ def test_first_100_iterates(name):
                     assert np.linalg.norm(g[key]) <= 1e-300, (k, key)
                 else:
                     assert rel(g[key], r_) <= 1e-11, (k, key, rel(g[key], r_))
-
-
-def _compare_checks(gpu, orc, tol_rel=1e-6, limit=12):
-    """Same (k, kind, cause) sequence over the leading `limit` records until a decision
-    that is a near-tie (a restart criterion whose deciding quantity is within 1e-9
-    relative of its threshold).  Later records are not compared: the two solvers round
-    differently and over ~1e5 iterations the iterates drift apart far more than the
-    residuals they decide on, so only the final results are compared there."""
-    n = min(len(gpu), len(orc), limit)
-    assert n > 0
-    prev_rt = {}
-    for i in range(n):
-        g, o = gpu[i], orc[i]
-        assert int(g["k"]) == int(o["k"]) and int(g["kind"]) == int(o["kind"]), (i, g, o)
-        for key in ("err_p", "err_d", "err_gap", "Rt"):
-            if int(g["kind"]) & 1 or key == "Rt":
-                assert g[key] == pytest.approx(o[key], rel=tol_rel, abs=1e-13), (i, key, g[key], o[key])
-        r = int(o["r"])
-        if int(g["cause"]) != int(o["cause"]):
-            R0, Rt = o["R0"], o["Rt"]
-            gaps = [abs(Rt - 0.2 * R0), abs(Rt - 0.6 * R0), abs(Rt - prev_rt.get(r, R0))]
-            t_gap = abs((o["t"] + 1) - 0.2 * (o["k"] + 1))
-            assert min(gaps) <= 1e-9 * abs(R0) or t_gap < 1e-9, (i, g, o)
-            return i
-        prev_rt[r] = o["Rt"]
-        if int(g["cause"]) > 0:
-            assert g["sigma_next"] == pytest.approx(o["sigma_next"], rel=1e-5)
-    return n
+                    # entry by entry, relative to the entry, with a floor of 1e-6 ||.||_inf
+                    # for entries near zero (their error is set by the row sums' terms)
+                    worst[key] = max(worst.get(key, 0.0), elem(g[key], r_, 1e-6))
+                    assert elem(g[key], r_, 1e-6) <= 1e-9, (k, key, elem(g[key], r_, 1e-6))
+    print(name, "worst entrywise error (floor 1e-6 ||.||_inf):", worst)
 
 
 @pytest.mark.parametrize("seed", range(5))
@@ -169,7 +156,8 @@ def test_full_solve_tiny(seed):
     assert abs(res["info"]["primal_obj"] - ref["info"]["pobj"]) <= 1e-7 * abs(ref["info"]["pobj"])
     assert abs(ind["pobj"] - lp.planted_objective) <= 1e-7 * abs(lp.planted_objective)
     assert K.in_C(res["x"], lp.l, lp.u) and K.in_D(res["y"], lp.m1)
-    _compare_checks(checks, ref["checks"])
+    where = compare_decisions(checks, ref["checks"], 1e-8)
+    print(f"tiny seed {seed}: decisions equal over {where} of {len(ref['checks'])} records")
 
 
 def test_full_solve_with_power_method():
@@ -197,7 +185,8 @@ def test_full_solve_medium_small_scale():
     assert ind["kkt"] <= 1e-8 * (1 + 1e-6)
     assert abs(res["info"]["primal_obj"] - ref["info"]["pobj"]) <= 1e-7 * abs(ref["info"]["pobj"])
     assert abs(ind["pobj"] - lp.planted_objective) <= 1e-7 * abs(lp.planted_objective)
-    _compare_checks(checks, ref["checks"])
+    where = compare_decisions(checks, ref["checks"], 1e-8)
+    print(f"medium/100: decisions equal over {where} of {len(ref['checks'])} records")
 
 
 @pytest.mark.parametrize("name", ["one_by_one", "only_ineq", "only_eq", "long_rows"])
