@@ -24,6 +24,7 @@
 #include "hpr_device.cuh"
 #include "hpr_mlp.cuh"
 #include "hpr_small.cuh"
+#include "hpr_grid.cuh"
 
 #include <cuda_runtime.h>
 
@@ -177,6 +178,11 @@ struct hpr_ctx {
     double *small_out = nullptr;
     int small_cap = 0;
     hprsmall::SmallArgs *small_args = nullptr; // persistent path: device copy of its arguments
+    double *grid_partials = nullptr;          // persistent grid path: CTA sums, barrier state
+    hprgrid::GridBar *grid_bar = nullptr;
+    int grid_ctas_used = 0;                   // CTAs of the last persistent grid solve
+    int64_t grid_ctas_env = 0;                // HPR_GRID_CTAS: CTA count of that path (0: by size)
+    int64_t fault_barrier = 0;                // HPR_FAULT_BARRIER=n: a CTA skips barrier n-1
     bool batched = false;         // owned by a batch: solved only through hpr_batch_solve
     std::vector<hpr_check_record> checks;
     std::string err;
@@ -434,7 +440,8 @@ void free_all(hpr_ctx *c)
                    c->l_s, c->u_s, c->l_o, c->u_o, c->x, c->x0, c->xhat, c->xbar,
                    c->zbar, c->dx, c->y, c->y0, c->ybar, c->dy, c->xo, c->yo, c->zo,
                    c->partials, c->scal, c->ctl, c->pctl, c->trace, c->policy_wb, c->policy_w32,
-                   c->policy_x, c->policy_q, c->small_recs, c->small_out, c->small_args};
+                   c->policy_x, c->policy_q, c->small_recs, c->small_out, c->small_args,
+                   c->grid_partials, c->grid_bar};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->scal_h) cudaFreeHost(c->scal_h);
@@ -1223,7 +1230,7 @@ static int check_options(hpr_ctx *ctx, const hpr_options *o)
     if (o->reflect != 0 && o->reflect != 1) return fail_arg(ctx, HPR_ERR_ARG, "reflect must be 0 or 1");
     if (o->autotune != 0 && o->autotune != 1) return fail_arg(ctx, HPR_ERR_ARG, "autotune must be 0 or 1");
     if (o->sigma_policy < 0 || o->sigma_policy > 2) return fail_arg(ctx, HPR_ERR_ARG, "sigma_policy must be 0, 1 or 2");
-    if (o->persistent < 0 || o->persistent > 2) return fail_arg(ctx, HPR_ERR_ARG, "persistent must be 0, 1 or 2");
+    if (o->persistent < 0 || o->persistent > 3) return fail_arg(ctx, HPR_ERR_ARG, "persistent must be 0, 1, 2 or 3");
     if (o->pdl != 0 && o->pdl != 1) return fail_arg(ctx, HPR_ERR_ARG, "pdl must be 0 or 1");
     if (!(o->policy_margin >= 0.0) || o->policy_margin > 100.0)
         return fail_arg(ctx, HPR_ERR_ARG, "policy_margin must be in [0, 100]");
@@ -1252,7 +1259,9 @@ int hpr_create(hpr_ctx **out, const hpr_csr *A1, const hpr_csr *A2, const double
         return code;
     };
     for (auto &kv : {std::make_pair("HPR_FAULT_ALLOC", &ctx->fault_alloc),
-                     std::make_pair("HPR_FAULT_NAN_CHECK", &ctx->fault_nan_check)}) {
+                     std::make_pair("HPR_FAULT_NAN_CHECK", &ctx->fault_nan_check),
+                     std::make_pair("HPR_FAULT_BARRIER", &ctx->fault_barrier),
+                     std::make_pair("HPR_GRID_CTAS", &ctx->grid_ctas_env)}) {
         const char *v = std::getenv(kv.first);
         *kv.second = v ? std::max(0LL, std::atoll(v)) : 0;
     }

@@ -536,6 +536,77 @@ int solve_small(hpr_ctx *ctx, double tol)
     return small_collect(ctx);
 }
 
+// ---------------------------------------------------------------- persistent grid path
+// Mid-size LPs: one cooperative launch of G CTAs (hpr_grid.cuh).  Its CTA count follows the
+// FP64 work of an iteration (the part's FP64 issue rate bounds each SM's share): about
+// GRID_FP64_PER_CTA warp instructions per CTA, at most one CTA per SM.  The default path
+// choice takes it between the single-CTA path's limit and GRID_FP64_MAX.
+constexpr double GRID_FP64_PER_CTA = 100.0;
+constexpr double GRID_FP64_MAX = 0.0;
+constexpr uint64_t GRID_BUDGET_NS = 5000000000ull;       // 5 s: longest wait at a barrier
+constexpr uint64_t GRID_FAULT_BUDGET_NS = 200000ull;     // 200 us when a skip is injected
+
+const char *grid_unfit(const hpr_ctx *ctx, bool forced)
+{
+    const hpr_options &o = ctx->opt;
+    if (o.precision != 0) return "the FP32 form";
+    if (o.trace_iters > 0) return "tracing";
+    if (o.time_limit_s > 0.0) return "a time limit";
+    if (o.sigma_policy != 0) return "a sigma policy";
+    if (!forced && small_fp64_per_iter(ctx) > GRID_FP64_MAX) return "enough work per iteration to fill the GPU from launches";
+    return nullptr;
+}
+
+int solve_grid(hpr_ctx *ctx, double tol)
+{
+    using namespace hprgrid;
+    hprsmall::SmallArgs A;
+    size_t smem = 0;
+    int st = small_prepare(ctx, tol, A, &smem);   // solve state, record and result buffers
+    if (st) return st;
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_grid, NT, 0));
+    if (per_sm < 1) return fail_arg(ctx, HPR_ERR_CUDA, "the persistent grid kernel does not fit on an SM");
+    const int maxG = std::max(1, ctx->num_sms);
+    int G = (int)std::ceil(small_fp64_per_iter(ctx) / GRID_FP64_PER_CTA);
+    if (ctx->grid_ctas_env > 0) G = (int)std::min<int64_t>(ctx->grid_ctas_env, maxG);
+    G = std::max(2, std::min(G, maxG));
+    if (!ctx->grid_partials) DALLOC(ctx->grid_partials, (int64_t)NQG * maxG);
+    if (!ctx->grid_bar) DALLOC(ctx->grid_bar, 1);
+    GridArgs P{};
+    P.m = A.m; P.n = A.n; P.G = G;
+    P.A = A.A; P.T = A.T;
+    P.ineq = A.ineq;
+    P.b = A.b; P.c = A.c; P.l = A.l; P.u = A.u; P.wr = A.wr; P.wc = A.wc;
+    P.beta_b = A.beta_b; P.beta_c = A.beta_c; P.norm_b = A.norm_b; P.norm_c = A.norm_c;
+    P.tol = A.tol; P.alpha1 = A.alpha1; P.alpha2 = A.alpha2; P.alpha3 = A.alpha3; P.sigma0 = A.sigma0;
+    P.lambda_fixed = A.lambda_fixed; P.power_tol = A.power_tol;
+    P.max_iter = A.max_iter; P.check_every = A.check_every; P.power_max_iter = A.power_max_iter;
+    P.seed = A.seed;
+    P.restart = A.restart; P.sigma_update = A.sigma_update; P.halpern = A.halpern; P.reflect = A.reflect;
+    P.perm_r = A.perm_r;
+    P.x = ctx->x; P.x0 = ctx->x0; P.xh = ctx->xhat; P.xb = ctx->xbar; P.zb = ctx->zbar; P.dx = ctx->dx;
+    P.y = ctx->y; P.y0 = ctx->y0; P.yb = ctx->ybar; P.dy = ctx->dy;
+    P.partials = ctx->grid_partials;
+    P.bar = ctx->grid_bar;
+    P.budget_ns = ctx->fault_barrier > 0 ? GRID_FAULT_BUDGET_NS : GRID_BUDGET_NS;
+    P.skip_cta = ctx->fault_barrier > 0 ? G - 1 : -1;
+    P.skip_at = ctx->fault_barrier > 0 ? (int)(ctx->fault_barrier - 1) : -1;
+    P.recs = A.recs; P.rec_cap = A.rec_cap; P.out = A.out;
+    CK(cudaMemsetAsync(ctx->grid_bar, 0, sizeof(GridBar), ctx->stream));
+    void *kargs[] = {&P};
+    CK(cudaLaunchCooperativeKernel((const void *)k_solve_grid, dim3(G), dim3(NT), kargs, 0, ctx->stream));
+    GridBar hb{};
+    CK(cudaMemcpyAsync(&hb, ctx->grid_bar, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->grid_ctas_used = G;
+    if (hb.err)
+        return fail_arg(ctx, HPR_ERR_DEVICE_TIMEOUT,
+                        "persistent grid solve: a wait at grid barrier " + std::to_string(hb.where) +
+                            " ran out of its time budget; every CTA returned");
+    return small_collect(ctx);
+}
+
 }  // namespace
 
 extern "C" {
@@ -546,11 +617,18 @@ int hpr_solve(hpr_ctx *ctx, double tol)
     if (!(tol > 0.0)) return fail_arg(ctx, HPR_ERR_ARG, "tol must be > 0");
     if (ctx->batched) return fail_arg(ctx, HPR_ERR_STATE, "the context belongs to a batch");
     cudaSetDevice(ctx->device);
-    if (ctx->opt.persistent) {
+    ctx->grid_ctas_used = 0;
+    if (ctx->opt.persistent == 1 || ctx->opt.persistent == 2) {
         const char *why = small_unfit(ctx, ctx->opt.persistent == 2);
         if (!why) return solve_small(ctx, tol);
         if (ctx->opt.persistent == 2)
             return fail_arg(ctx, HPR_ERR_ARG, std::string("persistent = 2 but the single-CTA path cannot run: ") + why);
+    }
+    if (ctx->opt.persistent == 1 || ctx->opt.persistent == 3) {
+        const char *why = grid_unfit(ctx, ctx->opt.persistent == 3);
+        if (!why) return solve_grid(ctx, tol);
+        if (ctx->opt.persistent == 3)
+            return fail_arg(ctx, HPR_ERR_ARG, std::string("persistent = 3 but the persistent grid path cannot run: ") + why);
     }
     int st = solve_begin(ctx, tol);
     if (st) return st;

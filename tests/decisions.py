@@ -96,9 +96,15 @@ def compare_decisions(gpu, orc, tol, tol_rel=1e-6, sigma_rule=True, max_iter=1 <
                         if (gm[key] <= 0) != (om[key] <= 0) and abs(om[key]) <= 2 * tol_rel * scale]
             assert straddle, ("divergence not at a near-tie", i, g, o)
             return i
-        for key in ("err_p", "err_d", "err_gap", "Rt"):
+        for key in ("err_p", "err_d", "pobj", "dobj", "Rt"):
             if int(g["kind"]) & 1 or key == "Rt":
                 assert g[key] == pytest.approx(o[key], rel=tol_rel, abs=1e-13), (i, key, g[key], o[key])
+        if int(g["kind"]) & 1:
+            # the relative gap |dobj - pobj| / (1 + |pobj| + |dobj|) cancels: its disagreement is
+            # bounded by the objectives' own disagreement (checked just above), not by its size
+            den = 1.0 + abs(o["pobj"]) + abs(o["dobj"])
+            bound = 2.0 * (abs(g["pobj"] - o["pobj"]) + abs(g["dobj"] - o["dobj"])) / den + 1e-13
+            assert abs(g["err_gap"] - o["err_gap"]) <= bound, (i, "err_gap", g["err_gap"], o["err_gap"], bound)
         if int(g["cause"]) > 0:
             assert g["sigma_next"] == pytest.approx(o["sigma_next"], rel=tol_rel), (i, g, o)
     assert len(gpu) == len(orc), "one solver stopped earlier without a divergent decision"
