@@ -258,6 +258,22 @@ int hpr_power_noalloc(int64_t m, int64_t n, const int32_t *A_row_ptr, const int3
                       const double *At_val, uint64_t seed, int64_t max_iter, double tol,
                       double *u, double *s, void *cuda_stream, double *lambda, int64_t *iters);
 
+/* Memory-system probe (no counterpart in the paper: a measurement helper for the roofline
+ * of the phase kernels, which are bound by HBM bandwidth for their streamed arrays and by
+ * the rate of random 8-byte gathers, each costing an L1 cache-tag lookup).  On the current
+ * device and `cuda_stream` (NULL: the legacy default stream), timed with CUDA events, best of
+ * five runs after one warm-up:
+ *   *read_gbs    a read-only stream of read_bytes bytes (16-byte loads, integer consumer, no
+ *                FP64 work) after L2 was filled with another buffer: GB/s;
+ *   *gather_gps  random 8-byte gathers from an L2-resident array of gather_len doubles
+ *                (indices hashed in registers, integer consumer): 1e9 gathers/s.
+ * read_bytes in [2^20, 2^34]; gather_len a power of two in [2^10, 2^28].  Allocates and frees
+ * its own device buffers (read_bytes + max(4 x L2 size, 256 MiB) + 8 gather_len bytes).
+ * Returns HPR_OK, HPR_ERR_ARG, HPR_ERR_NO_DEVICE, HPR_ERR_NOMEM or HPR_ERR_CUDA; detail in
+ * hpr_last_error(NULL). */
+int hpr_memory_probe(int64_t read_bytes, int64_t gather_len, void *cuda_stream, double *read_gbs,
+                     double *gather_gps);
+
 /* Layout of the context's sliced-ELL copies (no counterpart in the paper: a storage choice
  * of this library), after autotuning if asked: for A (index 0) and A^T (index 1) the
  * lanes-per-row bound, the work-unit size and the number of work units; any pointer may

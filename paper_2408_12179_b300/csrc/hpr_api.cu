@@ -610,26 +610,35 @@ EpiPrimal epi_primal(hpr_ctx *ctx)
     return p;
 }
 
+// the two phases of a normal iteration, as a solve launches them (programmatic dependent
+// launches)
+int launch_normal_x(hpr_ctx *ctx, int it)
+{
+    if (ctx->form == 1) return launch_sell_pdl(ctx, ctx->ST, epi_x32<false>(ctx, it));
+    return launch_sell_pdl(ctx, ctx->ST, epi_x<false>(ctx, it));
+}
+
+int launch_normal_y(hpr_ctx *ctx, int it)
+{
+    if (ctx->form == 1) return launch_sell_pdl(ctx, ctx->SA, epi_y32<false>(ctx, it));
+    return launch_sell_pdl(ctx, ctx->SA, epi_y<false>(ctx, it));
+}
+
 // one HPR iteration (phase X then phase Y).  store: the phases also store x_bar, z_bar,
 // y_bar, x - x_bar, y - y_bar; check: the two residual passes run and every check
 // quantity is reduced into scal slot `slot`.
 int enqueue_iteration(hpr_ctx *ctx, int it, bool store, bool check, int slot)
 {
     int st;
-    if (ctx->form == 1) {
-        if (store || check) {
-            if ((st = launch_sell(ctx, ctx->ST, epi_x32<true>(ctx, it)))) return st;
-            if ((st = launch_sell(ctx, ctx->SA, epi_y32<true>(ctx, it)))) return st;
-        } else {
-            if ((st = launch_sell_pdl(ctx, ctx->ST, epi_x32<false>(ctx, it)))) return st;
-            if ((st = launch_sell_pdl(ctx, ctx->SA, epi_y32<false>(ctx, it)))) return st;
-        }
+    if (ctx->form == 1 && (store || check)) {
+        if ((st = launch_sell(ctx, ctx->ST, epi_x32<true>(ctx, it)))) return st;
+        if ((st = launch_sell(ctx, ctx->SA, epi_y32<true>(ctx, it)))) return st;
     } else if (store || check) {
         if ((st = launch_sell(ctx, ctx->ST, epi_x<true>(ctx, it)))) return st;
         if ((st = launch_sell(ctx, ctx->SA, epi_y<true>(ctx, it)))) return st;
     } else {
-        if ((st = launch_sell_pdl(ctx, ctx->ST, epi_x<false>(ctx, it)))) return st;
-        if ((st = launch_sell_pdl(ctx, ctx->SA, epi_y<false>(ctx, it)))) return st;
+        if ((st = launch_normal_x(ctx, it))) return st;
+        if ((st = launch_normal_y(ctx, it))) return st;
     }
     if (!check) return HPR_OK;
     if ((st = launch_sell(ctx, ctx->ST, epi_dual(ctx)))) return st;
@@ -1384,3 +1393,4 @@ int hpr_power(hpr_ctx *ctx, double *lambda, int64_t *iters)
 #include "hpr_api_batch.cuh"
 #include "hpr_api_policy.cuh"
 #include "hpr_api_noalloc.cuh"
+#include "hpr_api_probe.cuh"

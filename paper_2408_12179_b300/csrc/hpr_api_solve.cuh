@@ -795,18 +795,20 @@ int hpr_time_iteration(hpr_ctx *ctx, int64_t reps, double *ms_x, double *ms_y, d
         cudaError_t ce = cudaEventCreate(&e);
         if (ce != cudaSuccess) { e = nullptr; rc = fail_cuda(ctx, ce, "hpr_time_iteration", __LINE__); break; }
     }
-    const bool f32 = ctx->opt.precision == 1;
+    const int form_saved = ctx->form;
+    ctx->form = ctx->opt.precision == 1 ? 1 : 0;
     if (rc == HPR_OK) rc = (cudaEventRecord(ev[0], s) == cudaSuccess) ? HPR_OK : HPR_ERR_CUDA;
     for (int64_t r = 0; r < total && rc == HPR_OK; ++r) {
-        rc = f32 ? launch_sell(ctx, ctx->ST, epi_x32<false>(ctx, 0))
-                 : launch_sell(ctx, ctx->ST, epi_x<false>(ctx, 0));
+        // the kernels of a normal iteration of a solve (an event between two launches makes
+        // the programmatic overlap between them a plain stream order)
+        rc = launch_normal_x(ctx, 0);
         if (rc) break;
         cudaEventRecord(ev[(size_t)(2 * r + 1)], s);
-        rc = f32 ? launch_sell(ctx, ctx->SA, epi_y32<false>(ctx, 0))
-                 : launch_sell(ctx, ctx->SA, epi_y<false>(ctx, 0));
+        rc = launch_normal_y(ctx, 0);
         if (rc) break;
         cudaEventRecord(ev[(size_t)(2 * r + 2)], s);
     }
+    ctx->form = form_saved;
     double tx = 0.0, ty = 0.0;
     if (rc == HPR_OK) {
         cudaError_t e = cudaEventSynchronize(ev.back());

@@ -5,8 +5,8 @@
 //
 // Algorithm 2 has two grid-wide dependencies per iteration: the y step (eq. update-y-2)
 // gathers all of x_hat = 2 x_bar - x, and the next x step (eq. update-x) gathers all of y.
-// Between kernel launches the stream provides them; here a software grid barrier does (an
-// arrival counter and a generation word in device memory).  LPs too large for one SM but
+// Between kernel launches the stream provides them; here a software grid barrier does (a
+// monotonic arrival counter in device memory).  LPs too large for one SM but
 // too small to fill the GPU spend most of a launched iteration in launch latency; two
 // barriers cost less.
 //
@@ -41,8 +41,7 @@ constexpr int NQG = 10;                      // check quantities (as the single-
 
 // barrier state in device memory (zeroed by the host before every launch)
 struct GridBar {
-    unsigned int count;                      // arrivals at the current barrier
-    unsigned int gen;                        // barriers completed
+    unsigned long long count;                // arrivals so far: barrier nb completes at (nb+1) G
     int err;                                 // 1: a wait ran out of budget
     int where;                               // the barrier number at which it did
 };
@@ -69,10 +68,10 @@ struct GridArgs {
     double *out;                             // hprsmall::SO_LEN values
 };
 
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
 {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -83,49 +82,39 @@ __device__ __forceinline__ int ld_relaxed(const int *p)
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned int *p, unsigned int v)
+__device__ __forceinline__ void add_release(unsigned long long *p)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
 }
 
-// Grid-wide barrier number `nb` (every CTA calls the barriers in the same order).  Returns
-// false on every thread of the CTA if any wait of the launch ran out of budget: the caller
-// then returns.  Ordering: the CTA barrier orders all threads' writes before thread 0's
-// fence and arrival; the last arrival releases the generation word; waiting thread 0s
-// acquire it, then a CTA barrier passes the order on to their threads.
+// Grid-wide barrier number `nb` (every CTA calls the barriers in the same order, once each):
+// thread 0 adds its arrival to a monotonic counter with release semantics and polls it with
+// acquire loads until all G CTAs have arrived at this barrier, (nb+1) G arrivals in all; the
+// CTA barriers before and after pass the order on to the other threads.  Every 64 polls it
+// checks the error word and its time budget.  Returns false on every thread of the CTA if a
+// wait of the launch ran out of budget: the caller then returns.
 __device__ __forceinline__ bool grid_sync(const GridArgs &P, int nb, int *s_ok)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         GridBar *B = P.bar;
         int ok = 1;
-        const unsigned int g = ld_acquire(&B->gen);
-        __threadfence();
-        bool last = false;
-        if (!(blockIdx.x == (unsigned)P.skip_cta && nb == P.skip_at)) {
-            const unsigned int a = atomicAdd(&B->count, 1u);
-            if (a == (unsigned)P.G - 1) {
-                atomicExch(&B->count, 0u);
-                __threadfence();
-                st_release(&B->gen, g + 1);
-                last = true;
-            }
-        }
-        if (!last) {
+        const unsigned long long target = (unsigned long long)(nb + 1) * (unsigned long long)P.G;
+        if (!(blockIdx.x == (unsigned)P.skip_cta && nb == P.skip_at)) add_release(&B->count);
+        if (ld_acquire(&B->count) < target) {
             const uint64_t t0 = hprsmall::now_ns();
-            for (;;) {
-                if (ld_acquire(&B->gen) != g) break;
-                if (ld_relaxed(&B->err)) { ok = 0; break; }
-                if (hprsmall::now_ns() - t0 > P.budget_ns) {
-                    if (atomicExch(&B->err, 1) == 0) B->where = nb;
-                    ok = 0;
-                    break;
+            unsigned polls = 0;
+            while (ld_acquire(&B->count) < target) {
+                if ((++polls & 63u) == 0) {
+                    if (ld_relaxed(&B->err)) { ok = 0; break; }
+                    if (hprsmall::now_ns() - t0 > P.budget_ns) {
+                        if (atomicExch(&B->err, 1) == 0) B->where = nb;
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(64);
             }
         }
-        if (ok && ld_relaxed(&B->err)) ok = 0;
-        __threadfence();
         *s_ok = ok;
     }
     __syncthreads();

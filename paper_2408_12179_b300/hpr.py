@@ -98,6 +98,7 @@ SIGNATURES = {
                                          ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, _D, _I64]),
     "hpr_get_layout": (ctypes.c_int, [ctypes.c_void_p, _I64, _D, _I64]),
+    "hpr_memory_probe": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, _D, _D]),
     "hpr_layout_plan": (ctypes.c_int, [ctypes.POINTER(hpr_csr), ctypes.c_int64, ctypes.c_double, _I64, _I64,
                                        _I64, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_uint8), _I32, _I32,
                                        _I32]),
@@ -278,6 +279,14 @@ def hpr_time_iteration(ctx, reps: int):
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().hpr_time_iteration(ctx, int(reps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), ctx)
     return a.value, b.value, c.value
+
+
+def memory_probe(read_bytes=72_000_000, gather_len=1 << 18, stream=None):
+    """(read-only stream GB/s, random-gather rate in 1e9/s) measured by the library's probe
+    kernels (see hpr_memory_probe in include/hpr.h)."""
+    r, g = ctypes.c_double(), ctypes.c_double()
+    _check(load().hpr_memory_probe(int(read_bytes), int(gather_len), stream, ctypes.byref(r), ctypes.byref(g)), None)
+    return r.value, g.value
 
 
 def hpr_power_noalloc(m, n, A_ptrs, At_ptrs, seed, max_iter, tol, u_ptr, s_ptr, stream=None):

@@ -274,3 +274,4 @@ def test_programmatic_launch_changes_nothing(precision):
     assert a["info"]["iters"] == b["info"]["iters"] and a["info"]["restarts"] == b["info"]["restarts"]
     for key in ("x", "y", "z"):
         assert np.array_equal(a[key], b[key]), key
+
