@@ -141,22 +141,15 @@ def aggregate(torch, dist, secs, iters, device):
     return float(t.item()), float(k.item())
 
 
-def read_bandwidth_probe(torch):
-    """Read-only HBM bandwidth of this GPU, measured live: a reduction over a 1 GiB FP64
-    tensor (reads 1 GiB, writes nothing), best of 5 with CUDA events.  Context for the
-    roofline: the iteration reads ~16x more bytes than it writes, and on this part a
-    read-only stream tops out well below the copy (read + write) figure used as peak."""
-    t = torch.ones(1 << 27, dtype=torch.float64, device="cuda")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    best = 1e30
-    for _ in range(6):
-        e0.record()
-        t.sum()
-        e1.record()
-        torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1))
-    del t
-    return (1 << 30) / (best * 1e-3) / 1e9
+def memory_ceilings(hpr, phase_bytes, stream):
+    """Ceilings measured live by the library's own probe kernels (integer consumers, no FP64
+    work): a read-only stream of the phase's size and of 1 GiB launched alone after L2 was
+    filled with other data, and the rate of random 8-byte gathers from an L2-resident array
+    (each costs an L1 cache-tag lookup).  Context for the roofline: a phase reads ~10x more
+    bytes than it writes, and every stored matrix entry gathers one vector entry."""
+    r_phase, g_rate = hpr.memory_probe(int(max(phase_bytes, 1 << 20)), 1 << 18, stream)
+    r_big, _ = hpr.memory_probe(1 << 30, 1 << 18, stream)
+    return {"read_gbs_phase_size": r_phase, "read_gbs_1GiB": r_big, "gather_g_per_s": g_rate}
 
 
 # the Section 4.2 ablation: DR, + restart & Halpern (HDR, fixed sigma), + sigma update (HDR),
@@ -217,6 +210,22 @@ def config_dict(args, lp):
             "precision": "fp64" if args.precision == 0 else "fp32 form, fp64 below kkt 1e-5",
             "variant": args.variant,
             "l2": l2}
+
+
+def oracle_one_core(args, iters):
+    """The oracle on ONE host core (OMP_NUM_THREADS=1 in a child process, as the CPU plan asks
+    beside the all-core figure): HPR iterations/s over `iters` iterations of the workload."""
+    code = ("import json, sys; sys.path.insert(0, %r); import oracle; import bench; "
+            "lp = bench.workload(bench.parse_args(%r)); "
+            "r = oracle.solve(lp, max_iter=%d, lambda_fixed=1.0, checks_cap=16, **bench.VARIANTS[%r]); "
+            "print(json.dumps(r['info']['seconds']))") % (ROOT, sys.argv[1:], iters, args.variant)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        secs = float(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    return {"value": iters / secs, "unit": "iter/s", "cores": 1, "sample": f"{iters} oracle iterations, one thread"}
 
 
 def run_reference(args):
@@ -444,13 +453,22 @@ def run_ours(args):
     secs, all_iters = aggregate(torch, dist if world > 1 else None, ms / 1e3, iters, "cuda")
     value = all_iters / secs
 
-    # live per-kernel timing (CUDA events on the solver's stream) for the roofline
+    # live per-kernel timing (CUDA events on the solver's stream) for the roofline: each phase
+    # launched alone (an event between the phases), and the in-solve time per iteration (the
+    # 150-iteration periods run as CUDA graphs with programmatic launches, checks included,
+    # power method left out) split between the phases in the same proportion
     ms_x, ms_y, ms_it = solver.time_iteration(50)
-    read_ceiling = read_bandwidth_probe(torch)
+    in_graph_ms = statistics.median((i["solve_time_s"] - i["power_time_s"]) * 1e3 / max(1, i["iters"])
+                                    for i in infos)
     bx, by = algorithmic_bytes(lp.nnz, lp.n, lp.m, args.precision)
     peak, peak_kind = measured_peak()
     dom, dom_ms, dom_bytes = ("k_phase_x", ms_x, bx) if ms_x >= ms_y else ("k_phase_y", ms_y, by)
+    dom_in_graph_ms = in_graph_ms * dom_ms / (ms_x + ms_y)
+    ceil = memory_ceilings(hpr, dom_bytes, stream.cuda_stream)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    # every stored entry of the phase's matrix gathers one entry of the other vector
+    gathers = lp.nnz
+    gather_rate = gathers / (dom_ms * 1e-3) / 1e9
     traffic = None
     if (NCU_TRAFFIC["source_sha1"] == kernel_source_sha1() and args.workload == "medium" and args.scale == 1.0
             and args.seed == 0 and args.precision == 0 and args.variant == "hpr"):
@@ -496,12 +514,14 @@ def run_ours(args):
         import oracle
 
         it = args.sample_iters
-        r = oracle.solve(lp, max_iter=it, lambda_fixed=infos[-1]["lambda"], checks_cap=16,
-                         **VARIANTS[args.variant])
+        r = oracle.solve(lp, max_iter=it, lambda_fixed=1.0, checks_cap=16, **VARIANTS[args.variant])
         cpu = {"value": it / r["info"]["seconds"], "unit": "iter/s",
                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
-               "sample": f"{it} oracle iterations (one check) of the full workload, lambda fixed to the "
-                         f"GPU power-method value"}
+               "sample": f"{it} oracle iterations (one check) of the full workload, lambda fixed to 1 "
+                         f"(as the reference arm; lambda does not change the cost of an iteration)"}
+        one = oracle_one_core(args, max(10, it // 10))
+        if one is not None:
+            cpu["one_core"] = one
 
     t8 = [i["solve_time_s"] for i in infos]
     t4 = [i["time_to_1e4_s"] for i in infos]
@@ -525,8 +545,13 @@ def run_ours(args):
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_kind, "bytes_per_launch": dom_bytes,
                      "ms_per_launch": dom_ms, "ms_phase_x": ms_x, "ms_phase_y": ms_y,
-                     "read_only_ceiling_gbs": read_ceiling,
-                     "frac_of_read_only_ceiling": achieved / read_ceiling},
+                     "in_graph": {"ms_per_iteration": in_graph_ms, "ms_per_launch": dom_in_graph_ms,
+                                  "achieved": dom_bytes / (dom_in_graph_ms * 1e-3) / 1e9,
+                                  "frac": dom_bytes / (dom_in_graph_ms * 1e-3) / 1e9 / peak},
+                     "ceilings": ceil,
+                     "frac_of_read_stream_same_size": achieved / ceil["read_gbs_phase_size"],
+                     "gathers_per_launch": gathers, "gather_g_per_s": gather_rate,
+                     "frac_of_gather_rate": gather_rate / ceil["gather_g_per_s"]},
         "gpu_launches": int(sum(i["launches"] for i in infos)),
         "e2e": e2e,
         "clocks": clocks,
@@ -538,6 +563,44 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_forms(args):
+    """The FP32 form against plain FP64 on the same instances: `count` seeded medium planted LPs
+    at `scale`, each solved to tol with precision 0 and with precision 1 in the same context
+    (power method included in both).  value = geometric mean of the time ratios (FP32 form /
+    FP64) over the instances where both converged; one record per instance beside it."""
+    import torch
+
+    from paper_2408_12179_b300 import hpr, lpgen
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    hpr.load()
+    rows = []
+    for seed in range(args.seed, args.seed + args.count):
+        lp = lpgen.planted_medium(seed, args.scale)
+        row = {"seed": seed, "m": lp.m, "n": lp.n, "nnz": lp.nnz}
+        with hpr.Solver(lp, max_iter=args.max_iter, persistent=0) as s:
+            for prec in (0, 1):
+                s.set_options(precision=prec)
+                I = s.solve(args.tol)["info"]
+                row[f"p{prec}"] = dict(iters=int(I["iters"]), seconds=I["solve_time_s"], status=int(I["status"]),
+                                       iters_fp32=int(I["iters_fp32"]), kkt=I["kkt"])
+        rows.append(row)
+    ok = [r for r in rows if r["p0"]["status"] == 0 and r["p1"]["status"] == 0]
+    ratios = [r["p1"]["seconds"] / r["p0"]["seconds"] for r in ok]
+    gm = math.exp(sum(math.log(x) for x in ratios) / max(len(ratios), 1)) if ratios else None
+    line = {"metric": "time to KKT<=tol, FP32 form / plain FP64 (geometric mean over instances)",
+            "value": gm, "unit": "ratio", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{args.count} medium planted LPs at scale {args.scale} (seeds {args.seed}..)",
+                       "tol": args.tol, "max_iter": args.max_iter},
+            "instances": len(rows), "both_converged": len(ok), "fp32_form_faster": sum(x < 1 for x in ratios),
+            "total_fp64_s": sum(r["p0"]["seconds"] for r in ok),
+            "total_fp32_form_s": sum(r["p1"]["seconds"] for r in ok), "rows": rows}
+    print(json.dumps(line), flush=True)
 
 
 def run_tiny(args):
@@ -650,7 +713,7 @@ def run_tiny(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
@@ -667,10 +730,11 @@ def main():
                     help="0: FP64; 1: FP32 form, then FP64 below KKT 1e-5")
     ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true",
                     help="also time one plain FP64 solve and report it beside the chosen form")
-    ap.add_argument("--workload", choices=["medium", "mcf", "batch", "qap", "tiny"], default="medium",
+    ap.add_argument("--workload", choices=["medium", "mcf", "batch", "qap", "tiny", "forms"], default="medium",
                     help="medium sparse planted LP (default), the min-cost multicommodity flow LP "
-                         "(1M nodes at scale 1), or a batch of uneven planted LPs solved in one "
-                         "batched run (m log-uniform in [500, 50000 * scale])")
+                         "(1M nodes at scale 1), a batch of uneven planted LPs solved in one "
+                         "batched run (m log-uniform in [500, 50000 * scale]), or the FP32 form "
+                         "against FP64 on --count medium planted LPs at --scale")
     ap.add_argument("--count", type=int, default=None,
                     help="LPs in the batch workload (default 512) or the tiny workload (default 100)")
     ap.add_argument("--qap-n", dest="qap_n", type=int, default=30,
@@ -688,11 +752,18 @@ def main():
                     help="ablation variant of Section 4.2 (default: HPR-LP itself)")
     ap.add_argument("--lambda-fixed", dest="lambda_fixed", type=float, default=0.0,
                     help="use this lambda instead of the power method (short profiling runs)")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.count is None:
-        args.count = 100 if args.workload == "tiny" else 512
+        args.count = {"tiny": 100, "forms": 8}.get(args.workload, 512)
+    return args
+
+
+def main():
+    args = parse_args()
     if args.workload == "tiny" and args.impl == "ours":
         run_tiny(args)
+    elif args.workload == "forms":
+        run_forms(args)
     elif args.impl == "reference" and args.workload == "batch":
         run_reference_batch(args)
     elif args.workload == "batch":
