@@ -159,6 +159,8 @@ typedef struct {
     int64_t iters_fp32;           /* iterations run in the FP32 form (precision 1) */
     int64_t policy_decisions;     /* restarts whose sigma the policy network chose */
     int64_t policy_fallbacks;     /* restarts that fell back to Algorithm 3 (sigma_policy 2) */
+    double power_rel_change;      /* power method: |lambda_k - lambda_{k-1}| / lambda_k at its last
+                                     step (above power_tol when it stopped at power_max_iter) */
 } hpr_info;
 
 /* One evaluation of the restart / termination quantities.  kind: 1 = periodic check,

@@ -141,6 +141,7 @@ struct hpr_ctx {
     size_t ctl_bytes = 0;
     int ctl_cap = 0;
     PowCtl *pctl = nullptr, *pctl_h = nullptr;
+    unsigned *pow_ticket = nullptr;   // last-CTA tickets of the two power-method launches
     double *trace = nullptr;
     int64_t trace_n = 0;
     int64_t trace_written = 0;
@@ -170,6 +171,7 @@ struct hpr_ctx {
     double lambda = 0.0;
     int64_t power_iters = 0;
     double power_time = 0.0;
+    double power_rel_change = 0.0;   // the power method's last relative change of lambda
     hpr_info info{};
     SolveState ss;
     __nv_bfloat16 *policy_wb = nullptr;   // sigma policy network (BF16), its input and output
@@ -441,7 +443,7 @@ void free_all(hpr_ctx *c)
                    c->zbar, c->dx, c->y, c->y0, c->ybar, c->dy, c->xo, c->yo, c->zo,
                    c->partials, c->scal, c->ctl, c->pctl, c->trace, c->policy_wb, c->policy_w32,
                    c->policy_x, c->policy_q, c->small_recs, c->small_out, c->small_args,
-                   c->grid_partials, c->grid_bar};
+                   c->grid_partials, c->grid_bar, c->pow_ticket};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->scal_h) cudaFreeHost(c->scal_h);
@@ -707,43 +709,43 @@ int run_power(hpr_ctx *ctx)
 {
     const int64_t m = ctx->m;
     const int gm = (int)((m + TB - 1) / TB);
-    // u (m) in dy, s = A^T u (n) in dx, w = A s (m) in ybar
-    double *u = ctx->dy, *s = ctx->dx, *w = ctx->ybar;
+    // w (m) in dy: the start vector, then A s; s = A^T w / ||w|| (n) in dx
+    double *u = ctx->dy, *s = ctx->dx;
     k_pow_start<<<gm, TB, 0, ctx->stream>>>((int)m, ctx->opt.seed, ctx->perm_r, u, ctx->partials,
                                              ctx->pstride);
     CKL();
     int st = launch_reduce(ctx, {{Q_V2, gm}}, ctx->scal);
     if (st) return st;
-    double *invp = ctx->scal + Q_V2B;
-    k_inv_sqrt_scalar<<<1, 1, 0, ctx->stream>>>(ctx->scal, Q_V2, invp);
-    CKL();
-    k_scale_vec<<<grid_for(m), 256, 0, ctx->stream>>>((int)m, u, u, nullptr, invp);
-    CKL();
-
     PowCtl pc{};
     pc.tol = ctx->opt.power_tol;
     pc.max_iter = (int)std::max<int64_t>(1, ctx->opt.power_max_iter);
     *ctx->pctl_h = pc;
     CK(cudaMemcpyAsync(ctx->pctl, ctx->pctl_h, sizeof(PowCtl), cudaMemcpyHostToDevice, ctx->stream));
+    // the first step normalises the start vector inside its row sums: inv = 1 / ||w||
+    k_inv_sqrt_scalar<<<1, 1, 0, ctx->stream>>>(ctx->scal, Q_V2, &ctx->pctl->inv);
+    CKL();
 
+    // two launches a step (EpiPowT, EpiPowA): each folds the previous normalisation or
+    // reduction into its own row sums / last CTA
+    EpiPowT et{};
+    et.xa = et.xb = u; et.q[0] = Q_S2; et.partials = ctx->partials; et.pstride = ctx->pstride; et.out = s;
+    et.pc = ctx->pctl;
+    EpiPowA ea{};
+    ea.xa = ea.xb = s; ea.q[0] = Q_W2; ea.partials = ctx->partials; ea.pstride = ctx->pstride; ea.out = u;
+    ea.pc = ctx->pctl;
+    auto launch_pow = [&](const SellDev &M, auto e, unsigned *ticket) -> int {
+        if (M.rows == 0) return HPR_OK;
+        k_sell_pow<<<M.grid, SELL_TB, 0, ctx->stream>>>(sell_of(M, false, &ctx->pctl->done), e, ticket);
+        CKL();
+        ctx->launches += 1;
+        return HPR_OK;
+    };
     auto enqueue_steps = [&](int steps) -> int {
         for (int k = 0; k < steps; ++k) {
-            int r = launch_sell(ctx, ctx->ST, epi_norm(ctx, u, s, Q_S2), &ctx->pctl->done);
+            int r = launch_pow(ctx->ST, et, ctx->pow_ticket);
             if (r) return r;
-            r = launch_reduce(ctx, {{Q_S2, ctx->ST.rows ? ctx->ST.grid : 0}}, ctx->scal, &ctx->pctl->done);
+            r = launch_pow(ctx->SA, ea, ctx->pow_ticket + 1);
             if (r) return r;
-            k_pow_after_s<<<1, 1, 0, ctx->stream>>>(ctx->pctl, ctx->scal);
-            CKL();
-            r = launch_sell(ctx, ctx->SA, epi_norm(ctx, s, w, Q_W2), &ctx->pctl->done);
-            if (r) return r;
-            r = launch_reduce(ctx, {{Q_W2, ctx->SA.rows ? ctx->SA.grid : 0}}, ctx->scal, &ctx->pctl->done);
-            if (r) return r;
-            k_pow_after_w<<<1, 1, 0, ctx->stream>>>(ctx->pctl, ctx->scal);
-            CKL();
-            k_scale_vec<<<grid_for(m), 256, 0, ctx->stream>>>((int)m, w, u, ctx->pctl, nullptr);
-            CKL();
-            k_pow_finish<<<1, 1, 0, ctx->stream>>>(ctx->pctl);
-            CKL();
         }
         return HPR_OK;
     };
@@ -764,13 +766,12 @@ int run_power(hpr_ctx *ctx)
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaGraphInstantiate", __LINE__);
     }
-    ctx->launches += 3;   // start vector, 1/norm, normalisation (+1 for the reduction above)
+    ctx->launches += 2;   // start vector, 1/norm (+1 for the reduction above)
     for (int64_t done_steps = 0; done_steps <= ctx->opt.power_max_iter; done_steps += BATCH) {
         if (ctx->opt.use_graph) {
-            ctx->launches += (int64_t)BATCH * 8;
+            ctx->launches += (int64_t)BATCH * 2;
             CK(cudaGraphLaunch(ctx->pow_graph, ctx->stream));
         } else {
-            ctx->launches += (int64_t)BATCH * 4;   // the 2 SpMVs and 2 reductions count themselves
             int r = enqueue_steps(BATCH);
             if (r) return r;
         }
@@ -780,6 +781,7 @@ int run_power(hpr_ctx *ctx)
     }
     ctx->lambda = ctx->pctl_h->lam;
     ctx->power_iters = ctx->pctl_h->k;
+    ctx->power_rel_change = ctx->pctl_h->rel_change;
     if (!std::isfinite(ctx->lambda) || !(ctx->lambda > 0.0))
         return fail_arg(ctx, HPR_ERR_NUMERIC, "power method returned a non-positive lambda");
     return HPR_OK;
@@ -1037,6 +1039,8 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     DALLOC(ctx->partials, (int64_t)NQ * ctx->pstride);
     DALLOC(ctx->scal, 2 * NQ);
     DALLOC(ctx->pctl, 1);
+    DALLOC(ctx->pow_ticket, 2);
+    CK(cudaMemsetAsync(ctx->pow_ticket, 0, sizeof(unsigned) * 2, ctx->stream));
     CKA(cudaMallocHost((void **)&ctx->scal_h, sizeof(double) * 2 * NQ));
     CKA(cudaMallocHost((void **)&ctx->pctl_h, sizeof(PowCtl)));
     int st = ensure_ctl(ctx, (int)std::min<int64_t>(ctx->opt.check_every, ctx->opt.max_iter));

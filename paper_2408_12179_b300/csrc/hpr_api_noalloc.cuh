@@ -19,7 +19,7 @@ namespace {
 constexpr int NA_SLOTS = 1024;                           // CTAs per reduction, at most
 constexpr int NA_PARTIALS = NQ * NA_SLOTS;               // per-CTA partial sums
 constexpr int NA_SCAL = NA_PARTIALS;                     // NQ reduced scalars
-constexpr int NA_CTL = NA_SCAL + NQ;                     // PowCtl (6 doubles)
+constexpr int NA_CTL = NA_SCAL + NQ;                     // PowCtl (7 doubles)
 constexpr int NA_INV = NA_CTL + 8;                       // 1 / ||u0||
 constexpr int NA_DOUBLES = NA_INV + 8;                   // 16,432 doubles = 131,456 bytes
 

@@ -98,6 +98,7 @@ int solve_begin(hpr_ctx *ctx, double tol)
         ctx->lambda = o.lambda_fixed;
         ctx->power_iters = 0;
         ctx->power_time = 0.0;
+        ctx->power_rel_change = 0.0;
     } else {
         st = run_power(ctx);
         if (st) return st;
@@ -390,6 +391,7 @@ int solve_finish(hpr_ctx *ctx)
     I.solve_time_s = total; I.power_time_s = ctx->power_time;
     I.time_to_1e4_s = S.time_1e4; I.iters_to_1e4 = S.iters_1e4;
     I.iters = S.k; I.restarts = S.r; I.power_iters = ctx->power_iters;
+    I.power_rel_change = ctx->power_rel_change;
     I.n_checks = (int64_t)ctx->checks.size(); I.launches = ctx->launches; I.status = S.status;
     I.iters_fp32 = S.iters_fp32;
     I.policy_decisions = S.policy_decisions;
@@ -499,6 +501,7 @@ int small_collect(hpr_ctx *ctx)
     ctx->lambda = h[SO_LAMBDA];
     ctx->power_iters = (int64_t)h[SO_POWER_ITERS];
     ctx->power_time = h[SO_POWER_S];
+    ctx->power_rel_change = h[SO_POWER_REL];
     S.lambda = h[SO_LAMBDA];
     S.k = (int64_t)h[SO_ITERS]; S.r = (int64_t)h[SO_RESTARTS]; S.sigma = h[SO_SIGMA];
     S.status = (int)h[SO_STATUS];

@@ -73,6 +73,7 @@ struct DevCtl {
 struct PowCtl {
     double lam, lam_prev, inv, tol;
     int k, done, max_iter, stop_after;
+    double rel_change;    // |lambda_k - lambda_{k-1}| / lambda_k of the last step (k > 1)
 };
 
 // ------------------------------------------------------------------ block reduction
@@ -688,6 +689,111 @@ struct EpiNorm {
         }
     }
 };
+
+// power method on A A^* (Section 4.1), two launches a step.  Step k: s = inv * A^T w (w is
+// the previous step's A s, or the start vector, and inv its reciprocal norm, so the
+// normalisation u = w / ||w|| rides in the row sums) with lambda_k = ||s||^2; then w = A s
+// and inv = 1 / ||w||.  The last CTA of each launch to finish adds the CTA partial sums in
+// a fixed order and takes the step's scalar decisions (convergence of lambda, the step
+// cap, a zero w) on its thread 0.
+struct EpiPowT {
+    using Val = double;
+    static constexpr int NV = 1, NP = 1;
+    const double *xa, *xb;       // gathered: w
+    int q[1];
+    double *partials;
+    int pstride;
+    double *out;                 // s
+    PowCtl *pc;
+    double inv;
+    struct Pre { int unused; };
+    __device__ __forceinline__ void load() { inv = pc->inv; }
+    __device__ __forceinline__ Pre prefetch(int) const { return Pre{0}; }
+    __device__ __forceinline__ void row(int j, bool act, const double *s, const Pre &, double *part) const
+    {
+        if (act) {
+            const double t = s[0] * inv;
+            out[j] = t;
+            part[0] = fma(t, t, part[0]);
+        }
+    }
+    // lambda_k = ||s||^2; stop when |lambda_k - lambda_{k-1}| <= tol lambda_k
+    __device__ __forceinline__ void finish(double sum) const
+    {
+        pc->k += 1;
+        pc->lam = sum;
+        if (pc->k > 1) pc->rel_change = fabs(sum - pc->lam_prev) / sum;
+        if (pc->k > 1 && fabs(sum - pc->lam_prev) <= pc->tol * sum) {
+            pc->done = 1;
+            return;
+        }
+        pc->lam_prev = sum;
+        if (pc->k >= pc->max_iter) pc->stop_after = 1;
+    }
+};
+
+struct EpiPowA {
+    using Val = double;
+    static constexpr int NV = 1, NP = 1;
+    const double *xa, *xb;       // gathered: s
+    int q[1];
+    double *partials;
+    int pstride;
+    double *out;                 // w
+    PowCtl *pc;
+    struct Pre { int unused; };
+    __device__ __forceinline__ void load() {}
+    __device__ __forceinline__ Pre prefetch(int) const { return Pre{0}; }
+    __device__ __forceinline__ void row(int i, bool act, const double *s, const Pre &, double *part) const
+    {
+        if (act) {
+            out[i] = s[0];
+            part[0] = fma(s[0], s[0], part[0]);
+        }
+    }
+    // inv = 1 / ||w|| for the next step (a zero w ends the method), and the step cap
+    __device__ __forceinline__ void finish(double sum) const
+    {
+        const double nw = sqrt(sum);
+        if (!(nw > 0.0)) {
+            pc->done = 1;
+            return;
+        }
+        pc->inv = 1.0 / nw;
+        if (pc->stop_after) pc->done = 1;
+    }
+};
+
+// A power-method launch: the phase kernel's row sums, then the last CTA to finish (a
+// ticket counter, reset by that CTA) sums the CTA partials in CTA order and calls finish.
+template <class E>
+__global__ void __launch_bounds__(SELL_TB, SELL_CTAS_PER_SM) k_sell_pow(SellArgs S, E e, unsigned *ticket)
+{
+    __shared__ double red[SELL_WARPS];
+    __shared__ bool last;
+    if (S.skip && *S.skip) return;
+    E ee = e;
+    ee.load();
+    const int run = blockIdx.x * SELL_WARPS + (threadIdx.x >> 5);
+    double part[1] = {0.0};
+    sell_unit(S, ee, run, part);
+    const double t = block_sum<SELL_TB>(part[0], red);
+    if (threadIdx.x == 0) {
+        ee.partials[ee.q[0] * ee.pstride + blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double sum = 0.0;
+    for (int g = threadIdx.x; g < (int)gridDim.x; g += SELL_TB) sum += __ldcg(ee.partials + ee.q[0] * ee.pstride + g);
+    sum = block_sum<SELL_TB>(sum, red);
+    if (threadIdx.x == 0) {
+        ee.finish(sum);
+        *ticket = 0u;
+    }
+}
 
 // ------------------------------------------------------------------ final reduction
 struct RedSpec {

@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
     // time): u in dy, s = A^T w / ||w|| in dx, w = A s in yb
     double lambda = P.lambda_fixed;
     int64_t piters = 0;
+    double prel = 0.0;
     if (!(lambda > 0.0)) {
         double p[1] = {0.0};
         for (int i = blockIdx.x * NT + tid; i < m; i += G * NT) {
@@ -257,6 +258,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
             grid_sums_then<2>(P.partials, G, [&](const double *sum) {
                 const double l = sum[0], prev = sc[1];
                 sc[1] = l;
+                if (k > 1) sc[2] = fabs(l - prev) / l;
                 if ((k > 1 && fabs(l - prev) <= P.power_tol * l) || k >= P.power_max_iter || !(sum[1] > 0.0))
                     s_flag = 1;
                 else
@@ -267,6 +269,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
         }
         lambda = sc[1];
         piters = k;
+        prel = k > 1 ? sc[2] : 0.0;
     }
     const uint64_t t_power = now_ns();
 
@@ -496,6 +499,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
         o[SO_KKT] = kkt; o[SO_T1E4] = t1e4; o[SO_I1E4] = (double)i1e4; o[SO_NREC] = (double)nrec;
         o[SO_POWER_S] = 1e-9 * (double)(t_power - t_start);
         o[SO_TOTAL_S] = 1e-9 * (double)(now_ns() - t_start);
+        o[SO_POWER_REL] = prel;
     }
 }
 

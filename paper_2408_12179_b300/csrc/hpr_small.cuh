@@ -55,7 +55,7 @@ struct SmallArgs {
 
 enum {
     SO_ITERS, SO_RESTARTS, SO_STATUS, SO_LAMBDA, SO_POWER_ITERS, SO_SIGMA, SO_POBJ, SO_DOBJ, SO_ERRP,
-    SO_ERRD, SO_GAP, SO_KKT, SO_T1E4, SO_I1E4, SO_NREC, SO_POWER_S, SO_TOTAL_S, SO_LEN
+    SO_ERRD, SO_GAP, SO_KKT, SO_T1E4, SO_I1E4, SO_NREC, SO_POWER_S, SO_TOTAL_S, SO_POWER_REL, SO_LEN
 };
 
 __device__ __forceinline__ uint64_t now_ns()
@@ -174,7 +174,7 @@ __device__ __forceinline__ void cta_sums_then(double (&v)[NV], int nact, double 
 // a step and no FP64 work outside the warps that own rows.  (The last step's A s is not
 // needed; it keeps the step uniform.)
 __device__ double power_small(const SmallArgs &P, double *w, double *s, double *red, double *sc, int *flag,
-                              int64_t *iters)
+                              int64_t *iters, double *rel_change)
 {
     const int tid = threadIdx.x;
     const int act_m = owner_warps((P.m + 31) / 32), actA = owner_warps(P.A.nslices),
@@ -213,6 +213,7 @@ __device__ double power_small(const SmallArgs &P, double *w, double *s, double *
         cta_sums_then<2>(q, act, red, [&](const double *sum) {
             const double l = sum[0], prev = sc[1];
             sc[1] = l;
+            if (k > 1) sc[2] = fabs(l - prev) / l;
             if ((k > 1 && fabs(l - prev) <= P.power_tol * l) || k >= P.power_max_iter || !(sum[1] > 0.0))
                 *flag = 1;
             else
@@ -222,6 +223,7 @@ __device__ double power_small(const SmallArgs &P, double *w, double *s, double *
     }
     lam = sc[1];
     *iters = k;
+    *rel_change = k > 1 ? sc[2] : 0.0;
     return lam;
 }
 
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(NT) k_solve_small(const SmallArgs *__restrict_
     const int act = actA > actT ? actA : actT;
     __shared__ double red[10 * 32];
     __shared__ double sums[10];
-    __shared__ double sc[2];
+    __shared__ double sc[3];
     __shared__ int pflag;
     __shared__ double sc_in[2];
     __shared__ double bc_sigma, bc_ha, bc_hb, bc_ils;    // this iteration's scalars (thread 0 sets them)
@@ -303,7 +305,8 @@ __global__ void __launch_bounds__(NT) k_solve_small(const SmallArgs *__restrict_
     // ---- lambda of T1 = lambda I - A A^* (power method, counted in the solve time)
     double lambda = P.lambda_fixed;
     int64_t piters = 0;
-    if (!(lambda > 0.0)) lambda = power_small(P, yb, x, red, sc, &pflag, &piters);
+    double prel = 0.0;
+    if (!(lambda > 0.0)) lambda = power_small(P, yb, x, red, sc, &pflag, &piters, &prel);
     const uint64_t t_power = now_ns();
 
     // ---- origin start, sigma_0 (Section 4.1)
@@ -522,6 +525,7 @@ __global__ void __launch_bounds__(NT) k_solve_small(const SmallArgs *__restrict_
         o[SO_KKT] = kkt; o[SO_T1E4] = t1e4; o[SO_I1E4] = (double)i1e4; o[SO_NREC] = (double)nrec;
         o[SO_POWER_S] = 1e-9 * (double)(t_power - t_start);
         o[SO_TOTAL_S] = 1e-9 * (double)(now_ns() - t_start);
+        o[SO_POWER_REL] = prel;
     }
 }
 

