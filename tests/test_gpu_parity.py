@@ -282,8 +282,7 @@ def test_programmatic_launch_changes_nothing(precision):
 def test_power_method_reports_its_last_change():
     """The power method's last relative change of lambda is reported: at most power_tol when
     it converged, above it when it stopped at the step cap."""
-    lp = lpgen.planted_medium(0, 0.01)
-    for cap, converged in ((5000, True), (3, False)):
+    for lp, cap, converged in ((lpgen.planted_tiny(0), 5000, True), (lpgen.planted_medium(0, 0.01), 3, False)):
         with hpr.Solver(lp, persistent=0, power_max_iter=cap, max_iter=150) as s:
             info = s.solve(1e-8)["info"]
         assert info["power_iters"] <= cap
