@@ -290,3 +290,28 @@ def test_power_method_reports_its_last_change():
             assert info["power_iters"] < cap and 0 < info["power_rel_change"] <= 1e-10
         else:
             assert info["power_iters"] == cap and info["power_rel_change"] > 1e-10
+
+
+def test_full_size_medium_solve_matches_the_oracle_solution():
+    """The benchmark workload itself (medium planted LP, m = 200k, n = 500k, ~5.2M nonzeros,
+    seed 0) solved to KKT <= 1e-8 on the default path, as the benchmark times it: the final
+    objective within 1e-7 relative of the oracle's solve of the same LP to 1e-8 (stored in
+    tests/golden/medium_lp_seed0.json by tests/golden/make_medium_solution.py, which calls only
+    the oracle) and of the planted optimum, and the KKT residual of the returned (x, y, z)
+    evaluated independently on the original LP <= 1e-8."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "medium_lp_seed0.json")))
+    assert g["status"] == 0 and g["kkt"] <= 1e-8
+    lp = lpgen.planted_medium(0, 1.0)
+    assert (lp.m, lp.n, lp.nnz) == (g["m"], g["n"], g["nnz"])
+    res = hpr.solve(lp, tol=1e-8)
+    assert res["status"] == hpr.HPR_OK
+    ind = K.kkt(lp, res["x"], res["y"], res["z"])
+    assert ind["kkt"] <= 1e-8 * (1 + 1e-6), ind
+    assert abs(res["info"]["primal_obj"] - g["pobj"]) <= 1e-7 * abs(g["pobj"])
+    assert abs(ind["pobj"] - g["planted_objective"]) <= 1e-7 * abs(g["planted_objective"])
+    assert K.in_C(res["x"], lp.l, lp.u) and K.in_D(res["y"], lp.m1)
+    print(f"full-size medium LP: {res['info']['iters']} iterations (oracle {g['iters']}), "
+          f"objective {res['info']['primal_obj']!r} vs oracle {g['pobj']!r}")
