@@ -537,6 +537,7 @@ def run_ours(args):
         "iters_to_kkt_1e-8": infos[-1]["iters"], "iters_to_kkt_1e-4": infos[-1]["iters_to_1e4"],
         "status": hpr.hpr_status_str(int(infos[-1]["status"])), "final_kkt": infos[-1]["kkt"],
         "restarts": infos[-1]["restarts"], "power_iters": infos[-1]["power_iters"],
+        "power_rel_change": infos[-1]["power_rel_change"],
         "iters_fp32": infos[-1]["iters_fp32"],
         "effective_hbm_gbs": value * (bx + by) / 1e9,
         "effective_hbm_frac": value * (bx + by) / 1e9 / peak,

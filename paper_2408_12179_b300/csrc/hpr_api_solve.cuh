@@ -113,6 +113,8 @@ int solve_begin(hpr_ctx *ctx, double tol)
     CK(cudaMemsetAsync(ctx->y0, 0, sizeof(double) * m, s));
     CK(cudaMemsetAsync(ctx->x32, 0, sizeof(float) * n, s));
     CK(cudaMemsetAsync(ctx->y32, 0, sizeof(float) * m, s));
+    CK(cudaMemsetAsync(ctx->x032, 0, sizeof(float) * n, s));
+    CK(cudaMemsetAsync(ctx->y032, 0, sizeof(float) * m, s));
     ctx->form = (int)o.precision;
     S.sigma = o.sigma0;
     S.status = HPR_MAX_ITER;
@@ -334,7 +336,7 @@ int period_after(hpr_ctx *ctx, double elapsed)
     if (widen) ctx->form = 0;
     if (restart && ctx->form == 1) {
         k_restart32<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->xbar, ctx->ybar, ctx->x32,
-                                                    ctx->x0, ctx->y32, ctx->y0);
+                                                    ctx->x0, ctx->y32, ctx->y0, ctx->x032, ctx->y032);
         CKL();
         ctx->launches += 1;
     } else if (restart) {

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace hprdev {
 
 constexpr int TB = 256;                 // threads per CTA (vector, reduction kernels)
@@ -151,6 +153,8 @@ struct Acc<double> {
     __device__ __forceinline__ void merge(const Acc &o) { a += o.a; }
     __device__ __forceinline__ void xor_reduce(int o) { a += __shfl_xor_sync(0xffffffffu, a, o); }
     __device__ __forceinline__ double value() const { return a; }
+    template <class S>
+    __device__ __forceinline__ S value_as() const { return a; }
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
@@ -187,6 +191,13 @@ struct Acc<float> {
         merge(t);
     }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    // the row sum as FP32 (the FP32 form's normal iterations: no FP64 instruction at all)
+    template <class S>
+    __device__ __forceinline__ S value_as() const
+    {
+        if constexpr (sizeof(S) == 4) return __fadd_rn(hi, lo);
+        else return value();
+    }
 };
 
 struct SellArgs {
@@ -222,10 +233,11 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
 {
     constexpr int NV = E::NV;
     using V = typename E::Val;
+    using Sm = typename E::Sum;                  // type of the row sums the epilogue takes
     const int lane = threadIdx.x & 31;
     bool waited = false;
     int buf_r0 = 0, buf_n = 0;                   // rows [buf_r0, buf_r0 + buf_n) hold sums
-    double buf0 = 0.0, buf1 = 0.0;               // lane t: sum of row buf_r0 + t
+    Sm buf0 = Sm(0), buf1 = Sm(0);               // lane t: sum of row buf_r0 + t
     typename E::Pre pre{};
     const int s_beg = run < S.nruns ? S.wstart[run] : 0;
     const int s_end = run < S.nruns ? S.wstart[run + 1] : 0;
@@ -236,7 +248,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
         const int steps = (S.sptr[s + 1] - base) >> 5;
         if (buf_n + nrows > 32) {                 // run started inside a group: flush early
             const int j = min(buf_r0 + lane, S.rows - 1);
-            const double sums[2] = {buf0, buf1};
+            const Sm sums[2] = {buf0, buf1};
             ee.row(j, lane < buf_n, sums, pre, part);
             buf_n = 0;
         }
@@ -316,8 +328,8 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
         }
         // row q of this slice (held by lanes q*L ...) moves to lane buf_n + q
         const int src = (int)(((unsigned)(lane - buf_n) << lg) & 31u);
-        const double m0 = __shfl_sync(0xffffffffu, a0.value(), src);
-        const double m1 = NV == 2 ? __shfl_sync(0xffffffffu, b0.value(), src) : 0.0;
+        const Sm m0 = __shfl_sync(0xffffffffu, a0.template value_as<Sm>(), src);
+        const Sm m1 = NV == 2 ? __shfl_sync(0xffffffffu, b0.template value_as<Sm>(), src) : Sm(0);
         if (lane >= buf_n && lane < buf_n + nrows) {
             buf0 = m0;
             buf1 = m1;
@@ -325,7 +337,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
         buf_n += nrows;
         if (buf_n == 32 || s + 1 == s_end) {      // a full group (or the end of the run)
             const int j = min(buf_r0 + lane, S.rows - 1);
-            const double sums[2] = {buf0, buf1};
+            const Sm sums[2] = {buf0, buf1};
             ee.row(j, lane < buf_n, sums, pre, part);
             buf_n = 0;
         }
@@ -427,6 +439,7 @@ __global__ void __launch_bounds__(TB) k_reduce_multi(const RedTask *__restrict__
 template <bool CHECK>
 struct EpiX {
     using Val = double;
+    using Sum = double;
     static constexpr int NV = 1, NP = CHECK ? 4 : 0;
     const double *xa, *xb;       // gathered: y
     int q[4];
@@ -480,6 +493,7 @@ struct EpiX {
 template <bool CHECK>
 struct EpiY {
     using Val = double;
+    using Sum = double;
     static constexpr int NV = 1, NP = CHECK ? 3 : 0;
     const double *xa, *xb;       // gathered: x_hat
     int q[3];
@@ -522,69 +536,93 @@ struct EpiY {
     }
 };
 
-// The FP32 form (FP32 stored values and FP32 iterates x, x_hat, y; FP64 anchors, data,
-// epilogue arithmetic and checks): phase X.  Row sums arrive in FP64 from the
-// double-float accumulators; x and x_hat are rounded to FP32 when stored.
+// The FP32 form (FP32 stored values and FP32 iterates x, x_hat, y): phase X.  Normal
+// iterations run the whole update in FP32 -- the row sum of the double-float accumulators
+// rounded to FP32, FP32 copies of c, l, u and of the anchor x0 -- so that no FP64
+// instruction is issued; check iterations (CHECK) take the FP64 row sum and FP64 data, as
+// the FP64 form does, and store the FP64 x_bar, z_bar of the check.
 template <bool CHECK>
 struct EpiX32 {
     using Val = float;
+    using Sum = typename std::conditional<CHECK, double, float>::type;
     static constexpr int NV = 1, NP = CHECK ? 4 : 0;
     const float *xa, *xb;        // gathered: y (FP32)
     int q[4];
     double *partials;
     int pstride;
-    const double *c, *l, *u, *x0;
+    const double *c, *l, *u, *x0;                 // FP64 data and anchor (checks)
+    const float *c32, *l32, *u32, *x032;          // their FP32 copies (normal iterations)
     float *x, *xhat;
     double *xbar, *zbar, *dx;
     const DevCtl *ctl;
     int it;
     int reflect;
     double sigma, ha, hb;
-    struct Pre { double x0, c, l, u; float x; };
+    float sigma32, ha32, hb32;
+    struct PreC { double x0, c, l, u; float x; };
+    struct PreF { float x0, c, l, u, x; };
+    using Pre = typename std::conditional<CHECK, PreC, PreF>::type;
     __device__ __forceinline__ void load()
     {
         sigma = ctl->sigma;
         ha = ctl->h[2 * it];
         hb = ctl->h[2 * it + 1];
+        sigma32 = (float)sigma;
+        ha32 = (float)ha;
+        hb32 = (float)hb;
     }
-    __device__ __forceinline__ Pre prefetch(int j) const { return Pre{x0[j], c[j], l[j], u[j], x[j]}; }
-    __device__ __forceinline__ void row(int j, bool act, const double *s, const Pre &p,
-                                        double *part) const
+    __device__ __forceinline__ Pre prefetch(int j) const
     {
-        const double xj = (double)p.x;
-        const double v = fma(sigma, s[0] - p.c, xj);
-        const double xb_ = clamp_lu(v, p.l, p.u);
-        const double xh = fma(2.0, xb_, -xj);
-        const double xn = fma(hb, reflect ? xh : xb_, ha * p.x0);
-        if (act) {
-            xhat[j] = (float)xh;
-            x[j] = (float)xn;
-        }
-        if (CHECK && act) {
-            const double zb = (xb_ - v) / sigma;
-            const double dd = xj - xb_;
-            xbar[j] = xb_;
-            zbar[j] = zb;
-            dx[j] = dd;
-            part[0] = fma(dd, dd, part[0]);
-            part[1] = fma(xb_ - p.x0, xb_ - p.x0, part[1]);
-            part[2] = fma(p.c, xb_, part[2]);
-            if (zb > 0.0) part[3] = fma(zb, p.l, part[3]);
-            else if (zb < 0.0) part[3] = fma(zb, p.u, part[3]);
+        if constexpr (CHECK) return Pre{x0[j], c[j], l[j], u[j], x[j]};
+        else return Pre{x032[j], c32[j], l32[j], u32[j], x[j]};
+    }
+    __device__ __forceinline__ void row(int j, bool act, const Sum *s, const Pre &p, double *part) const
+    {
+        if constexpr (!CHECK) {
+            const float v = __fmaf_rn(sigma32, __fsub_rn(s[0], p.c), p.x);
+            const float xb_ = fminf(fmaxf(v, p.l), p.u);               // Pi_C (l <= u)
+            const float xh = __fmaf_rn(2.0f, xb_, -p.x);
+            const float xn = __fmaf_rn(hb32, reflect ? xh : xb_, __fmul_rn(ha32, p.x0));
+            if (act) {
+                xhat[j] = xh;
+                x[j] = xn;
+            }
+        } else {
+            const double xj = (double)p.x;
+            const double v = fma(sigma, s[0] - p.c, xj);
+            const double xb_ = clamp_lu(v, p.l, p.u);
+            const double xh = fma(2.0, xb_, -xj);
+            const double xn = fma(hb, reflect ? xh : xb_, ha * p.x0);
+            if (act) {
+                xhat[j] = (float)xh;
+                x[j] = (float)xn;
+                const double zb = (xb_ - v) / sigma;
+                const double dd = xj - xb_;
+                xbar[j] = xb_;
+                zbar[j] = zb;
+                dx[j] = dd;
+                part[0] = fma(dd, dd, part[0]);
+                part[1] = fma(xb_ - p.x0, xb_ - p.x0, part[1]);
+                part[2] = fma(p.c, xb_, part[2]);
+                if (zb > 0.0) part[3] = fma(zb, p.l, part[3]);
+                else if (zb < 0.0) part[3] = fma(zb, p.u, part[3]);
+            }
         }
     }
 };
 
-// the FP32 form, phase Y
+// the FP32 form, phase Y (normal iterations in FP32 with FP32 copies of b and y0)
 template <bool CHECK>
 struct EpiY32 {
     using Val = float;
+    using Sum = typename std::conditional<CHECK, double, float>::type;
     static constexpr int NV = 1, NP = CHECK ? 3 : 0;
     const float *xa, *xb;        // gathered: x_hat (FP32)
     int q[3];
     double *partials;
     int pstride;
     const double *b, *y0;
+    const float *b32, *y032;
     float *y;
     double *ybar, *dy;
     const DevCtl *ctl;
@@ -592,30 +630,46 @@ struct EpiY32 {
     const unsigned char *ineq;
     int reflect;
     double inv_ls, ha, hb;
-    struct Pre { double b, y0; float y; unsigned char ineq; };
+    float inv_ls32, ha32, hb32;
+    struct PreC { double b, y0; float y; unsigned char ineq; };
+    struct PreF { float b, y0, y; unsigned char ineq; };
+    using Pre = typename std::conditional<CHECK, PreC, PreF>::type;
     __device__ __forceinline__ void load()
     {
         inv_ls = ctl->inv_ls;
         ha = ctl->h[2 * it];
         hb = ctl->h[2 * it + 1];
+        inv_ls32 = (float)inv_ls;
+        ha32 = (float)ha;
+        hb32 = (float)hb;
     }
-    __device__ __forceinline__ Pre prefetch(int i) const { return Pre{b[i], y0[i], y[i], ineq[i]}; }
-    __device__ __forceinline__ void row(int i, bool act, const double *s, const Pre &p,
-                                        double *part) const
+    __device__ __forceinline__ Pre prefetch(int i) const
     {
-        const double yi = (double)p.y;
-        double yb = fma(p.b - s[0], inv_ls, yi);
-        if (p.ineq) yb = pos_part(yb);
-        const double yh = fma(2.0, yb, -yi);
-        const double yn = fma(hb, reflect ? yh : yb, ha * p.y0);
-        if (act) y[i] = (float)yn;
-        if (CHECK && act) {
-            const double dd = yi - yb;
-            ybar[i] = yb;
-            dy[i] = dd;
-            part[0] = fma(dd, dd, part[0]);
-            part[1] = fma(yb - p.y0, yb - p.y0, part[1]);
-            part[2] = fma(p.b, yb, part[2]);
+        if constexpr (CHECK) return Pre{b[i], y0[i], y[i], ineq[i]};
+        else return Pre{b32[i], y032[i], y[i], ineq[i]};
+    }
+    __device__ __forceinline__ void row(int i, bool act, const Sum *s, const Pre &p, double *part) const
+    {
+        if constexpr (!CHECK) {
+            float yb = __fmaf_rn(__fsub_rn(p.b, s[0]), inv_ls32, p.y);
+            if (p.ineq) yb = __float_as_int(yb) < 0 ? 0.0f : yb;          // Pi_{R_+}
+            const float yh = __fmaf_rn(2.0f, yb, -p.y);
+            if (act) y[i] = __fmaf_rn(hb32, reflect ? yh : yb, __fmul_rn(ha32, p.y0));
+        } else {
+            const double yi = (double)p.y;
+            double yb = fma(p.b - s[0], inv_ls, yi);
+            if (p.ineq) yb = pos_part(yb);
+            const double yh = fma(2.0, yb, -yi);
+            const double yn = fma(hb, reflect ? yh : yb, ha * p.y0);
+            if (act) {
+                y[i] = (float)yn;
+                const double dd = yi - yb;
+                ybar[i] = yb;
+                dy[i] = dd;
+                part[0] = fma(dd, dd, part[0]);
+                part[1] = fma(yb - p.y0, yb - p.y0, part[1]);
+                part[2] = fma(p.b, yb, part[2]);
+            }
         }
     }
 };
@@ -623,6 +677,7 @@ struct EpiY32 {
 // dual residual of Section 4.1 in original-space weights w_c = beta_c / D_c
 struct EpiDual {
     using Val = double;
+    using Sum = double;
     static constexpr int NV = 1, NP = 1;
     const double *xa, *xb;       // gathered: y_bar
     int q[1];
@@ -645,6 +700,7 @@ struct EpiDual {
 // M-norm (eq. def:M with T1 = lambda I - A A^*)
 struct EpiPrimal {
     using Val = double;
+    using Sum = double;
     static constexpr int NV = 2, NP = 2;
     const double *xa, *xb;       // gathered: x_bar, x - x_bar
     int q[2];
@@ -672,6 +728,7 @@ struct EpiPrimal {
 // power method: out = M xin and the partial ||out||^2
 struct EpiNorm {
     using Val = double;
+    using Sum = double;
     static constexpr int NV = 1, NP = 1;
     const double *xa, *xb;
     int q[1];
@@ -698,6 +755,7 @@ struct EpiNorm {
 // cap, a zero w) on its thread 0.
 struct EpiPowT {
     using Val = double;
+    using Sum = double;
     static constexpr int NV = 1, NP = 1;
     const double *xa, *xb;       // gathered: w
     int q[1];
@@ -734,6 +792,7 @@ struct EpiPowT {
 
 struct EpiPowA {
     using Val = double;
+    using Sum = double;
     static constexpr int NV = 1, NP = 1;
     const double *xa, *xb;       // gathered: s
     int q[1];
@@ -834,20 +893,22 @@ __global__ void k_restart(int n, int m, const double *__restrict__ xbar,
     }
 }
 
-// restart in the FP32 form: x = (float) x_bar, x0 = x_bar, y likewise
+// restart in the FP32 form: x = (float) x_bar, x0 = x_bar and its FP32 copy, y likewise
 __global__ void k_restart32(int n, int m, const double *__restrict__ xbar,
                             const double *__restrict__ ybar, float *x, double *x0, float *y,
-                            double *y0)
+                            double *y0, float *x032, float *y032)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
         if (i < n) {
             const double v = xbar[i];
             x[i] = (float)v;
             x0[i] = v;
+            x032[i] = (float)v;
         } else {
             const double v = ybar[i - n];
             y[i - n] = (float)v;
             y0[i - n] = v;
+            y032[i - n] = (float)v;
         }
     }
 }
