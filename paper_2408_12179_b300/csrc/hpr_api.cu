@@ -130,6 +130,7 @@ struct hpr_ctx {
     float *x32 = nullptr, *xhat32 = nullptr, *y32 = nullptr;   // FP32-form iterates
     float *x032 = nullptr, *y032 = nullptr;   // FP32 copies of the anchors (FP32 form)
     float *cp32 = nullptr, *lp32 = nullptr, *up32 = nullptr, *bp32 = nullptr;   // and of the data
+    float *cp32lo = nullptr, *bp32lo = nullptr;   // c, b as double-float pairs (hi above, lo here)
     int form = 0;                 // form of the iterates during a solve (0 FP64, 1 FP32)
     double *xo = nullptr, *yo = nullptr, *zo = nullptr;
 
@@ -439,7 +440,7 @@ void free_all(hpr_ctx *c)
                    c->SA.srow, c->SA.sptr, c->SA.wstart, c->SA.slg, c->SA.col, c->SA.val, c->SA.src,
                    c->ST.srow, c->ST.sptr, c->ST.wstart, c->ST.slg, c->ST.col, c->ST.val, c->ST.src,
                    c->SA.val32, c->ST.val32, c->x32, c->xhat32, c->y32, c->x032, c->y032,
-                   c->cp32, c->lp32, c->up32, c->bp32,
+                   c->cp32, c->lp32, c->up32, c->bp32, c->cp32lo, c->bp32lo,
                    c->perm_r, c->perm_c, c->ineq, c->bp, c->cp, c->lp, c->up, c->wrp, c->wcp,
                    c->unperm, c->Dr, c->Dc, c->wr, c->wc, c->b_s, c->c_s,
                    c->l_s, c->u_s, c->l_o, c->u_o, c->x, c->x0, c->xhat, c->xbar,
@@ -570,7 +571,7 @@ EpiX32<CHECK> epi_x32(hpr_ctx *c, int it)
     e.q[0] = Q_DX2; e.q[1] = Q_XX0; e.q[2] = Q_CX; e.q[3] = Q_BND;
     e.partials = c->partials; e.pstride = c->pstride;
     e.c = c->cp; e.l = c->lp; e.u = c->up; e.x0 = c->x0;
-    e.c32 = c->cp32; e.l32 = c->lp32; e.u32 = c->up32; e.x032 = c->x032;
+    e.c32 = c->cp32; e.c32lo = c->cp32lo; e.l32 = c->lp32; e.u32 = c->up32; e.x032 = c->x032;
     e.x = c->x32; e.xhat = c->xhat32; e.xbar = c->xbar; e.zbar = c->zbar; e.dx = c->dx;
     e.ctl = c->ctl; e.it = it; e.reflect = (int)c->opt.reflect;
     return e;
@@ -584,7 +585,7 @@ EpiY32<CHECK> epi_y32(hpr_ctx *c, int it)
     e.q[0] = Q_DY2; e.q[1] = Q_YY0; e.q[2] = Q_BY;
     e.partials = c->partials; e.pstride = c->pstride;
     e.b = c->bp; e.y0 = c->y0; e.y = c->y32; e.ybar = c->ybar; e.dy = c->dy;
-    e.b32 = c->bp32; e.y032 = c->y032;
+    e.b32 = c->bp32; e.b32lo = c->bp32lo; e.y032 = c->y032;
     e.ctl = c->ctl; e.it = it; e.ineq = c->ineq; e.reflect = (int)c->opt.reflect;
     return e;
 }
@@ -1036,6 +1037,7 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     DALLOC(ctx->x32, n); DALLOC(ctx->xhat32, n); DALLOC(ctx->y32, m);
     DALLOC(ctx->x032, n); DALLOC(ctx->y032, m);
     DALLOC(ctx->cp32, n); DALLOC(ctx->lp32, n); DALLOC(ctx->up32, n); DALLOC(ctx->bp32, m);
+    DALLOC(ctx->cp32lo, n); DALLOC(ctx->bp32lo, m);
     DALLOC(ctx->Dr, m); DALLOC(ctx->Dc, n); DALLOC(ctx->wr, m); DALLOC(ctx->wc, n);
     DALLOC(ctx->b_s, m); DALLOC(ctx->c_s, n); DALLOC(ctx->l_s, n); DALLOC(ctx->u_s, n);
     DALLOC(ctx->l_o, n); DALLOC(ctx->u_o, n);
@@ -1122,10 +1124,10 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     k_permute<<<gn, 256, 0, s>>>(n, ctx->u_s, ctx->perm_c, ctx->up); CKL();
     k_permute<<<gn, 256, 0, s>>>(n, ctx->wc, ctx->perm_c, ctx->wcp); CKL();
     // FP32 copies of the data for the FP32 form's normal iterations (infinite bounds stay infinite)
-    k_narrow<<<gn, 256, 0, s>>>(n, ctx->cp, ctx->cp32); CKL();
+    k_split32<<<gn, 256, 0, s>>>(n, ctx->cp, ctx->cp32, ctx->cp32lo); CKL();
     k_narrow<<<gn, 256, 0, s>>>(n, ctx->lp, ctx->lp32); CKL();
     k_narrow<<<gn, 256, 0, s>>>(n, ctx->up, ctx->up32); CKL();
-    k_narrow<<<gm, 256, 0, s>>>(m, ctx->bp, ctx->bp32); CKL();
+    k_split32<<<gm, 256, 0, s>>>(m, ctx->bp, ctx->bp32, ctx->bp32lo); CKL();
     CK(cudaStreamSynchronize(s));
     if (ctx->opt.autotune) {
         int r1 = autotune_layout(ctx, false, rp, ci, pr, ipc);

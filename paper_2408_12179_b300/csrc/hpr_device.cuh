@@ -191,14 +191,29 @@ struct Acc<float> {
         merge(t);
     }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-    // the row sum as FP32 (the FP32 form's normal iterations: no FP64 instruction at all)
+    // the row sum as a normalised double-float pair (the FP32 form's normal iterations, which
+    // issue no FP64 instruction), or as FP64
     template <class S>
     __device__ __forceinline__ S value_as() const
     {
-        if constexpr (sizeof(S) == 4) return __fadd_rn(hi, lo);
-        else return value();
+        if constexpr (sizeof(S) == 8 && !std::is_same<S, double>::value) {
+            float h, l;
+            two_sum(hi, lo, h, l);
+            return S{h, l};
+        } else {
+            return value();
+        }
     }
 };
+
+// a - b of two double-float values (a_hi + a_lo, b_hi + b_lo), rounded once to FP32: the
+// difference keeps FP32 precision relative to ITSELF even when a and b nearly cancel
+__device__ __forceinline__ float df_sub(float ah, float al, float bh, float bl)
+{
+    float d, e;
+    two_sum(ah, -bh, d, e);
+    return __fadd_rn(d, __fadd_rn(e, __fsub_rn(al, bl)));
+}
 
 struct SellArgs {
     int rows;             // rows of the matrix (in the renumbered order)
@@ -225,6 +240,12 @@ __device__ __forceinline__ void dep_wait_and_trigger(const SellArgs &S)
     if ((int)blockIdx.x >= S.trigger_from) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+__device__ __forceinline__ double shfl_sum(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float2 shfl_sum(float2 v, int src)
+{
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
 // E supplies the value type Val (double or float) of the stored values and gathered
 // vectors, NV gathered vectors xa (, xb), NP partial sums (ids q[]), a Pre record of
 // epilogue operands (prefetch(j)) and row(j, act, s, pre, part) with FP64 row sums s.
@@ -237,7 +258,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
     const int lane = threadIdx.x & 31;
     bool waited = false;
     int buf_r0 = 0, buf_n = 0;                   // rows [buf_r0, buf_r0 + buf_n) hold sums
-    Sm buf0 = Sm(0), buf1 = Sm(0);               // lane t: sum of row buf_r0 + t
+    Sm buf0{}, buf1{};                           // lane t: sum of row buf_r0 + t
     typename E::Pre pre{};
     const int s_beg = run < S.nruns ? S.wstart[run] : 0;
     const int s_end = run < S.nruns ? S.wstart[run + 1] : 0;
@@ -328,8 +349,8 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
         }
         // row q of this slice (held by lanes q*L ...) moves to lane buf_n + q
         const int src = (int)(((unsigned)(lane - buf_n) << lg) & 31u);
-        const Sm m0 = __shfl_sync(0xffffffffu, a0.template value_as<Sm>(), src);
-        const Sm m1 = NV == 2 ? __shfl_sync(0xffffffffu, b0.template value_as<Sm>(), src) : Sm(0);
+        const Sm m0 = shfl_sum(a0.template value_as<Sm>(), src);
+        const Sm m1 = NV == 2 ? shfl_sum(b0.template value_as<Sm>(), src) : Sm{};
         if (lane >= buf_n && lane < buf_n + nrows) {
             buf0 = m0;
             buf1 = m1;
@@ -537,21 +558,23 @@ struct EpiY {
 };
 
 // The FP32 form (FP32 stored values and FP32 iterates x, x_hat, y): phase X.  Normal
-// iterations run the whole update in FP32 -- the row sum of the double-float accumulators
-// rounded to FP32, FP32 copies of c, l, u and of the anchor x0 -- so that no FP64
-// instruction is issued; check iterations (CHECK) take the FP64 row sum and FP64 data, as
-// the FP64 form does, and store the FP64 x_bar, z_bar of the check.
+// iterations run the update without a single FP64 instruction: the row sum arrives as the
+// accumulators' double-float pair, c as a double-float pair of FP32 values, and s - c is
+// formed by an error-free sum before it is rounded (the two nearly cancel near a solution:
+// rounding them first would turn the difference into noise); l, u and the anchor x0 are FP32
+// copies.  Check iterations (CHECK) take the FP64 row sum and FP64 data, as the FP64 form
+// does, and store the FP64 x_bar, z_bar of the check.
 template <bool CHECK>
 struct EpiX32 {
     using Val = float;
-    using Sum = typename std::conditional<CHECK, double, float>::type;
+    using Sum = typename std::conditional<CHECK, double, float2>::type;
     static constexpr int NV = 1, NP = CHECK ? 4 : 0;
     const float *xa, *xb;        // gathered: y (FP32)
     int q[4];
     double *partials;
     int pstride;
     const double *c, *l, *u, *x0;                 // FP64 data and anchor (checks)
-    const float *c32, *l32, *u32, *x032;          // their FP32 copies (normal iterations)
+    const float *c32, *c32lo, *l32, *u32, *x032;  // FP32 copies (normal iterations; c as hi + lo)
     float *x, *xhat;
     double *xbar, *zbar, *dx;
     const DevCtl *ctl;
@@ -560,7 +583,7 @@ struct EpiX32 {
     double sigma, ha, hb;
     float sigma32, ha32, hb32;
     struct PreC { double x0, c, l, u; float x; };
-    struct PreF { float x0, c, l, u, x; };
+    struct PreF { float x0, ch, cl, l, u, x; };
     using Pre = typename std::conditional<CHECK, PreC, PreF>::type;
     __device__ __forceinline__ void load()
     {
@@ -574,13 +597,14 @@ struct EpiX32 {
     __device__ __forceinline__ Pre prefetch(int j) const
     {
         if constexpr (CHECK) return Pre{x0[j], c[j], l[j], u[j], x[j]};
-        else return Pre{x032[j], c32[j], l32[j], u32[j], x[j]};
+        else return Pre{x032[j], c32[j], c32lo[j], l32[j], u32[j], x[j]};
     }
     __device__ __forceinline__ void row(int j, bool act, const Sum *s, const Pre &p, double *part) const
     {
         if constexpr (!CHECK) {
-            const float v = __fmaf_rn(sigma32, __fsub_rn(s[0], p.c), p.x);
-            const float xb_ = fminf(fmaxf(v, p.l), p.u);               // Pi_C (l <= u)
+            const float d = df_sub(s[0].x, s[0].y, p.ch, p.cl);             // A^T y - c
+            const float v = __fmaf_rn(sigma32, d, p.x);
+            const float xb_ = fminf(fmaxf(v, p.l), p.u);                    // Pi_C (l <= u)
             const float xh = __fmaf_rn(2.0f, xb_, -p.x);
             const float xn = __fmaf_rn(hb32, reflect ? xh : xb_, __fmul_rn(ha32, p.x0));
             if (act) {
@@ -611,18 +635,19 @@ struct EpiX32 {
     }
 };
 
-// the FP32 form, phase Y (normal iterations in FP32 with FP32 copies of b and y0)
+// the FP32 form, phase Y (normal iterations: b - A x_hat by an error-free sum of double-float
+// pairs, FP32 copies of y0)
 template <bool CHECK>
 struct EpiY32 {
     using Val = float;
-    using Sum = typename std::conditional<CHECK, double, float>::type;
+    using Sum = typename std::conditional<CHECK, double, float2>::type;
     static constexpr int NV = 1, NP = CHECK ? 3 : 0;
     const float *xa, *xb;        // gathered: x_hat (FP32)
     int q[3];
     double *partials;
     int pstride;
     const double *b, *y0;
-    const float *b32, *y032;
+    const float *b32, *b32lo, *y032;
     float *y;
     double *ybar, *dy;
     const DevCtl *ctl;
@@ -632,7 +657,7 @@ struct EpiY32 {
     double inv_ls, ha, hb;
     float inv_ls32, ha32, hb32;
     struct PreC { double b, y0; float y; unsigned char ineq; };
-    struct PreF { float b, y0, y; unsigned char ineq; };
+    struct PreF { float bh, bl, y0, y; unsigned char ineq; };
     using Pre = typename std::conditional<CHECK, PreC, PreF>::type;
     __device__ __forceinline__ void load()
     {
@@ -646,12 +671,13 @@ struct EpiY32 {
     __device__ __forceinline__ Pre prefetch(int i) const
     {
         if constexpr (CHECK) return Pre{b[i], y0[i], y[i], ineq[i]};
-        else return Pre{b32[i], y032[i], y[i], ineq[i]};
+        else return Pre{b32[i], b32lo[i], y032[i], y[i], ineq[i]};
     }
     __device__ __forceinline__ void row(int i, bool act, const Sum *s, const Pre &p, double *part) const
     {
         if constexpr (!CHECK) {
-            float yb = __fmaf_rn(__fsub_rn(p.b, s[0]), inv_ls32, p.y);
+            const float d = df_sub(p.bh, p.bl, s[0].x, s[0].y);            // b - A x_hat
+            float yb = __fmaf_rn(d, inv_ls32, p.y);
             if (p.ineq) yb = __float_as_int(yb) < 0 ? 0.0f : yb;          // Pi_{R_+}
             const float yh = __fmaf_rn(2.0f, yb, -p.y);
             if (act) y[i] = __fmaf_rn(hb32, reflect ? yh : yb, __fmul_rn(ha32, p.y0));
@@ -673,6 +699,17 @@ struct EpiY32 {
         }
     }
 };
+
+// hi + lo FP32 split of FP64 values: hi = fl32(v), lo = fl32(v - hi) (infinities: lo = 0)
+__global__ void k_split32(int64_t len, const double *__restrict__ src, float *hi, float *lo)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = src[i];
+        const float h = (float)v;
+        hi[i] = h;
+        lo[i] = isinf(v) ? 0.0f : (float)(v - (double)h);
+    }
+}
 
 // dual residual of Section 4.1 in original-space weights w_c = beta_c / D_c
 struct EpiDual {

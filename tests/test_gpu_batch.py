@@ -50,7 +50,9 @@ def test_batch_equals_solo_solves(precisions):
             st = b.stats()
         assert status == hpr.HPR_MAX_ITER            # the slow ones stop at the cap
         assert st["periods"] > 0 and st["fused_launches"] > 0
-        assert sum(r["status"] == hpr.HPR_OK for r in res) >= 4
+        print(precisions, [(lp.name or i, p, int(r["status"]), int(r["info"]["iters"]))
+                           for i, (lp, p, r) in enumerate(zip(lps, prec, res))])
+        assert sum(r["status"] == hpr.HPR_OK for r in res) >= 4   # converged LPs are compared too
         for lp, p, r in zip(lps, prec, res):
             solo = _solo(lp, precision=p, max_iter=CAP)
             assert r["status"] == solo["status"], lp.name

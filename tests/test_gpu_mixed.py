@@ -42,6 +42,23 @@ def test_fp32_phase_iterates_close_to_fp64_oracle(name):
     print(f"{name}: worst relative error of FP32-form iterates vs FP64 oracle over 100 iterations: {worst:.2e}")
 
 
+@pytest.mark.parametrize("name", ["tiny", "medium_1e-2"])
+def test_fp32_normal_iterations_close_to_fp64_oracle(name):
+    """The FP32 form's normal iterations (FP32 epilogue arithmetic, no tracing: a traced
+    iteration takes the FP64 check-mode epilogue) over 100 iterations without the switch:
+    the w_bar returned at the cap against the FP64 oracle's, within FP32 rounding."""
+    lp = lpgen.planted_tiny(0) if name == "tiny" else lpgen.planted_medium(0, 0.01)
+    N = 100
+    ref = oracle.solve(lp, max_iter=N)
+    lam = ref["info"]["lambda"]
+    res = hpr.solve(lp, tol=1e-12, max_iter=N, lambda_fixed=lam, precision=1, switch_tol=0.0, persistent=0)
+    assert res["status"] == hpr.HPR_MAX_ITER and res["info"]["iters_fp32"] == N
+    errs = {key: rel(res[key], ref[key]) for key in ("x", "y", "z")}
+    print(f"{name}: FP32-form normal iterations, relative error of w_bar after {N} iterations: {errs}")
+    for key in ("x", "y"):
+        assert errs[key] <= 2e-5, (key, errs[key])
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_switch_form_solves_tiny(seed):
     lp = lpgen.planted_tiny(seed)
