@@ -36,9 +36,9 @@ BATCH_METRIC = "HPR iterations/s summed over the LPs of the batch workload (LPs 
 # FP64; see profiles/), valid only for that workload and the kernel source they were
 # taken on.
 NCU_TRAFFIC = {
-    "source_sha1": "20c28fd31299cfc25da142959919d90d53146536",
-    "k_phase_x": 87993600,
-    "k_phase_y": 73059584,
+    "source_sha1": "782d35b2fe9c35b67484bea6bce22291802308b6",
+    "k_phase_x": 87568128,
+    "k_phase_y": 72345088,
 }
 
 

@@ -711,8 +711,56 @@ int ensure_ctl(hpr_ctx *ctx, int cap)
 
 // ---------------------------------------------------------------- power method
 
+double small_fp64_per_iter(const hpr_ctx *ctx);
+constexpr double SMALL_POWER_FP64_MAX = 600.0;
+constexpr size_t SMALL_POWER_SMEM_MAX = 200 * 1024;
+
+// the power method in one CTA (k_power_small) when the LP fits one SM and its FP64 work per
+// step is small: the same steps as the multi-CTA kernels, two block barriers a step instead
+// of two launches
+int run_power_small(hpr_ctx *ctx, bool *done)
+{
+    *done = false;
+    const size_t smem = sizeof(double) * (size_t)(ctx->m + ctx->n);
+    if (smem > SMALL_POWER_SMEM_MAX || small_fp64_per_iter(ctx) > SMALL_POWER_FP64_MAX) return HPR_OK;
+    hprsmall::SmallArgs A{};
+    auto mat_of = [](const SellDev &D) {
+        hprsmall::SmallMat M{};
+        M.nslices = D.nslices; M.entries = D.entries;
+        M.srow = D.srow; M.sptr = D.sptr; M.col = D.col; M.slg = D.slg; M.val = D.val;
+        return M;
+    };
+    A.m = (int)ctx->m; A.n = (int)ctx->n;
+    A.A = mat_of(ctx->SA); A.T = mat_of(ctx->ST);
+    A.seed = ctx->opt.seed; A.perm_r = ctx->perm_r;
+    A.power_tol = ctx->opt.power_tol;
+    A.power_max_iter = std::max<int64_t>(1, ctx->opt.power_max_iter);
+    if (!ctx->small_args) DALLOC(ctx->small_args, 1);
+    if (!ctx->small_out) DALLOC(ctx->small_out, hprsmall::SO_LEN);
+    CK(cudaMemcpyAsync(ctx->small_args, &A, sizeof A, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaFuncSetAttribute(hprsmall::k_power_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    hprsmall::k_power_small<<<1, hprsmall::NT, smem, ctx->stream>>>(ctx->small_args, ctx->small_out);
+    CKL();
+    ctx->launches += 1;
+    double h[3];
+    CK(cudaMemcpyAsync(h, ctx->small_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->lambda = h[0];
+    ctx->power_iters = (int64_t)h[1];
+    ctx->power_rel_change = h[2];
+    if (!std::isfinite(ctx->lambda) || !(ctx->lambda > 0.0))
+        return fail_arg(ctx, HPR_ERR_NUMERIC, "power method returned a non-positive lambda");
+    *done = true;
+    return HPR_OK;
+}
+
 int run_power(hpr_ctx *ctx)
 {
+    {
+        bool done = false;
+        int r = run_power_small(ctx, &done);
+        if (r || done) return r;
+    }
     const int64_t m = ctx->m;
     const int gm = (int)((m + TB - 1) / TB);
     // w (m) in dy: the start vector, then A s; s = A^T w / ||w|| (n) in dx

@@ -413,6 +413,7 @@ constexpr double SMALL_FP64_MAX = 600.0;
 
 double small_fp64_per_iter(const hpr_ctx *ctx)
 {
+    // one SM issues the FP64 work of an iteration (or of a power step, the same SpMVs)
     return (double)(ctx->SA.entries + ctx->ST.entries) / 32.0 + 8.0 * (double)(ctx->SA.nslices + ctx->ST.nslices);
 }
 

@@ -227,6 +227,26 @@ __device__ double power_small(const SmallArgs &P, double *w, double *s, double *
     return lam;
 }
 
+// The power method alone in one CTA, for LPs that fit one SM but whose iterations run on
+// the multi-CTA path (the FP32 form, tracing, a time limit, ...): w (m) and s (n) in
+// shared memory; out = {lambda, steps, last relative change of lambda}.
+__global__ void __launch_bounds__(NT) k_power_small(const SmallArgs *__restrict__ args, double *out)
+{
+    extern __shared__ double sh[];
+    const SmallArgs P = *args;
+    __shared__ double red[2 * 32];
+    __shared__ double sc[3];
+    __shared__ int flag;
+    int64_t iters = 0;
+    double rel = 0.0;
+    const double lam = power_small(P, sh, sh + P.m, red, sc, &flag, &iters, &rel);
+    if (threadIdx.x == 0) {
+        out[0] = lam;
+        out[1] = (double)iters;
+        out[2] = rel;
+    }
+}
+
 // Shared memory: n-vectors x, x0, xhat, xbar, zbar, dx; m-vectors y, y0, ybar, dy; with the
 // matrices: the values of A's and A^T's layouts, then their column indices and slice
 // tables, then their lane counts.
