@@ -22,15 +22,21 @@
  *   - a context is not thread-safe; separate contexts are independent.  A context
  *     uses the CUDA device that was current when it was created.
  *
- * Host-side fault injection, for testing the error paths without faulting a GPU (both
- * read from the environment by hpr_create; unset or 0: off):
+ * Host-side fault injection, for testing the error paths without faulting a GPU (read
+ * from the environment by hpr_create; unset or 0: off):
  *   HPR_FAULT_ALLOC=n      the n-th device or pinned host allocation that the context
  *                          makes (creation and solves counted together) reports
  *                          out-of-memory: the call returns HPR_ERR_NOMEM and a context
  *                          that exists stays valid for hpr_destroy;
  *   HPR_FAULT_NAN_CHECK=n  the check scalars of the n-th check period of the multi-CTA
  *                          path are replaced by NaN on the host after read-back: the solve
- *                          returns HPR_ERR_NUMERIC.
+ *                          returns HPR_ERR_NUMERIC;
+ *   HPR_FAULT_BARRIER=n    persistent grid path (persistent = 3): its last CTA skips its
+ *                          arrival at grid barrier n-1 and every wait's budget drops to
+ *                          200 us: the solve returns HPR_ERR_DEVICE_TIMEOUT.
+ * and, for measurements, HPR_GRID_CTAS=G: the CTA count of the persistent grid path (at
+ * most one per SM) and of the cluster path (at most 16; the largest resident cluster up to
+ * G is taken); unset or 0: chosen from the FP64 work of an iteration.
  */
 #ifndef HPR_H
 #define HPR_H
@@ -130,14 +136,25 @@ typedef struct {
     double policy_margin;     /* sigma_policy 2: a multiplier other than 1 (a = 2) is taken only
                                  when its predicted outcome beats a = 2's by more than this
                                  (log10 KKT units; default 0) */
-    int64_t persistent;       /* the persistent single-CTA path: one CTA of 1024 threads runs the
-                                 power method and all of Algorithm 2 on the device, iterates in
-                                 shared memory (LPs with 48 n + 32 m bytes <= 200 KB).  0 never;
-                                 1 (default) when the LP fits, the solve is plain FP64 without
-                                 tracing, time limit or policy, and one SM's share of FP64 work per
-                                 iteration is small enough to beat the multi-CTA path (stored
-                                 entries of A and A^T / 32 + 8 x their 32-row slices <= 600);
-                                 2 whenever it can run (HPR_ERR_ARG if it cannot) */
+    int64_t persistent;       /* the persistent paths, which run the power method and all of
+                                 Algorithm 2 in one launch (plain FP64 solves without tracing,
+                                 time limit or policy only):
+                                   single-CTA: one CTA of 1024 threads, iterates in shared memory
+                                   (LPs with 48 n + 32 m bytes <= 200 KB);
+                                   cluster: one thread-block cluster of up to 16 CTAs, hardware
+                                   cluster barriers between the two phases of an iteration, y and
+                                   x_hat replicated in every CTA's shared memory (LPs with
+                                   8 (m + n) bytes within one CTA's shared memory, ~227 KB);
+                                   grid: one cooperative launch of up to one CTA per SM, software
+                                   grid barriers with a bounded wait (HPR_ERR_DEVICE_TIMEOUT when
+                                   a wait runs out), gathers through L2.
+                                 0 never; 1 (default) the single-CTA path when the LP fits and
+                                 one SM's share of FP64 work per iteration is small enough to
+                                 beat the multi-CTA path (stored entries of A and A^T / 32 + 8 x
+                                 their 32-row slices <= 600), else the cluster path when it fits
+                                 and is expected to be faster, else the multi-CTA path;
+                                 2 / 4 / 3: the single-CTA / cluster / grid path whenever it can
+                                 run (HPR_ERR_ARG if it cannot) */
     int64_t pdl;              /* 1 (default): the two phases of a normal iteration are launched as
                                  programmatic dependents of the kernel before them, so that their
                                  set-up overlaps its tail; 0: plain stream order */
@@ -161,6 +178,10 @@ typedef struct {
     int64_t policy_fallbacks;     /* restarts that fell back to Algorithm 3 (sigma_policy 2) */
     double power_rel_change;      /* power method: |lambda_k - lambda_{k-1}| / lambda_k at its last
                                      step (above power_tol when it stopped at power_max_iter) */
+    int64_t path;                 /* the path the solve took, in hpr_options.persistent's codes:
+                                     0 multi-CTA (launches per iteration), 2 single-CTA, 3 grid,
+                                     4 cluster */
+    int64_t path_ctas;            /* CTAs of the persistent grid or cluster launch (else 0) */
 } hpr_info;
 
 /* One evaluation of the restart / termination quantities.  kind: 1 = periodic check,

@@ -25,6 +25,7 @@
 #include "hpr_mlp.cuh"
 #include "hpr_small.cuh"
 #include "hpr_grid.cuh"
+#include "hpr_cluster.cuh"
 
 #include <cuda_runtime.h>
 
@@ -145,6 +146,7 @@ struct hpr_ctx {
     int ctl_cap = 0;
     PowCtl *pctl = nullptr, *pctl_h = nullptr;
     unsigned *pow_ticket = nullptr;   // last-CTA tickets of the two power-method launches
+    int64_t pow_ticket_len = 0;
     double *trace = nullptr;
     int64_t trace_n = 0;
     int64_t trace_written = 0;
@@ -185,7 +187,8 @@ struct hpr_ctx {
     hprsmall::SmallArgs *small_args = nullptr; // persistent path: device copy of its arguments
     double *grid_partials = nullptr;          // persistent grid path: CTA sums, barrier state
     hprgrid::GridBar *grid_bar = nullptr;
-    int grid_ctas_used = 0;                   // CTAs of the last persistent grid solve
+    int grid_ctas_used = 0;                   // CTAs of the last persistent grid or cluster solve
+    int path_used = 0;                        // the path of the last solve (hpr_info.path)
     int64_t grid_ctas_env = 0;                // HPR_GRID_CTAS: CTA count of that path (0: by size)
     int64_t fault_barrier = 0;                // HPR_FAULT_BARRIER=n: a CTA skips barrier n-1
     bool batched = false;         // owned by a batch: solved only through hpr_batch_solve
@@ -590,13 +593,6 @@ EpiY32<CHECK> epi_y32(hpr_ctx *c, int it)
     return e;
 }
 
-EpiNorm epi_norm(hpr_ctx *c, const double *xin, double *out, int q)
-{
-    EpiNorm e{};
-    e.xa = xin; e.xb = xin; e.q[0] = q; e.partials = c->partials; e.pstride = c->pstride; e.out = out;
-    return e;
-}
-
 // residual passes of a check: dual (A^T y_bar) and primal with the M-norm cross term (A x_bar, A dx)
 EpiDual epi_dual(hpr_ctx *ctx)
 {
@@ -763,6 +759,18 @@ int run_power(hpr_ctx *ctx)
     }
     const int64_t m = ctx->m;
     const int gm = (int)((m + TB - 1) / TB);
+    // tickets of the two launches: a group counter per POW_GROUP CTAs and one over the groups
+    const int64_t tstride = 1 + ((int64_t)ctx->pstride + POW_GROUP - 1) / POW_GROUP;
+    if (ctx->pow_ticket_len < 2 * tstride) {
+        if (ctx->pow_graph) cudaGraphExecDestroy(ctx->pow_graph);
+        ctx->pow_graph = nullptr;
+        if (ctx->pow_ticket) cudaFree(ctx->pow_ticket);
+        ctx->pow_ticket = nullptr;
+        ctx->pow_ticket_len = 0;
+        DALLOC(ctx->pow_ticket, 2 * tstride);
+        CK(cudaMemsetAsync(ctx->pow_ticket, 0, sizeof(unsigned) * 2 * tstride, ctx->stream));
+        ctx->pow_ticket_len = 2 * tstride;
+    }
     // w (m) in dy: the start vector, then A s; s = A^T w / ||w|| (n) in dx
     double *u = ctx->dy, *s = ctx->dx;
     k_pow_start<<<gm, TB, 0, ctx->stream>>>((int)m, ctx->opt.seed, ctx->perm_r, u, ctx->partials,
@@ -798,7 +806,7 @@ int run_power(hpr_ctx *ctx)
         for (int k = 0; k < steps; ++k) {
             int r = launch_pow(ctx->ST, et, ctx->pow_ticket);
             if (r) return r;
-            r = launch_pow(ctx->SA, ea, ctx->pow_ticket + 1);
+            r = launch_pow(ctx->SA, ea, ctx->pow_ticket + tstride);
             if (r) return r;
         }
         return HPR_OK;
@@ -1040,7 +1048,6 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
         if ((r = check_kernel<EpiY<true>>(ctx))) return r;
         if ((r = check_kernel<EpiDual>(ctx))) return r;
         if ((r = check_kernel<EpiPrimal>(ctx))) return r;
-        if ((r = check_kernel<EpiNorm>(ctx))) return r;
         if ((r = check_kernel<EpiX32<false>>(ctx))) return r;
         if ((r = check_kernel<EpiX32<true>>(ctx))) return r;
         if ((r = check_kernel<EpiY32<false>>(ctx))) return r;
@@ -1096,8 +1103,6 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     DALLOC(ctx->partials, (int64_t)NQ * ctx->pstride);
     DALLOC(ctx->scal, 2 * NQ);
     DALLOC(ctx->pctl, 1);
-    DALLOC(ctx->pow_ticket, 2);
-    CK(cudaMemsetAsync(ctx->pow_ticket, 0, sizeof(unsigned) * 2, ctx->stream));
     CKA(cudaMallocHost((void **)&ctx->scal_h, sizeof(double) * 2 * NQ));
     CKA(cudaMallocHost((void **)&ctx->pctl_h, sizeof(PowCtl)));
     int st = ensure_ctl(ctx, (int)std::min<int64_t>(ctx->opt.check_every, ctx->opt.max_iter));
@@ -1305,7 +1310,7 @@ static int check_options(hpr_ctx *ctx, const hpr_options *o)
     if (o->reflect != 0 && o->reflect != 1) return fail_arg(ctx, HPR_ERR_ARG, "reflect must be 0 or 1");
     if (o->autotune != 0 && o->autotune != 1) return fail_arg(ctx, HPR_ERR_ARG, "autotune must be 0 or 1");
     if (o->sigma_policy < 0 || o->sigma_policy > 2) return fail_arg(ctx, HPR_ERR_ARG, "sigma_policy must be 0, 1 or 2");
-    if (o->persistent < 0 || o->persistent > 3) return fail_arg(ctx, HPR_ERR_ARG, "persistent must be 0, 1, 2 or 3");
+    if (o->persistent < 0 || o->persistent > 4) return fail_arg(ctx, HPR_ERR_ARG, "persistent must be 0, 1, 2, 3 or 4");
     if (o->pdl != 0 && o->pdl != 1) return fail_arg(ctx, HPR_ERR_ARG, "pdl must be 0 or 1");
     if (!(o->policy_margin >= 0.0) || o->policy_margin > 100.0)
         return fail_arg(ctx, HPR_ERR_ARG, "policy_margin must be in [0, 100]");

@@ -108,6 +108,8 @@ int batch_small(hpr_batch *b, double tol)
     }
     int status = HPR_OK;
     for (hpr_ctx *c : cs) {
+        c->grid_ctas_used = 0;
+        c->path_used = 2;
         const int st = small_collect(c);
         if (st < 0) return st;
         if (st != HPR_OK && status == HPR_OK) status = st;
@@ -466,6 +468,8 @@ int hpr_batch_solve(hpr_batch *b, double tol)
     }
     int worst = HPR_OK;
     for (hpr_ctx *c : cs) {
+        c->grid_ctas_used = 0;
+        c->path_used = 0;
         st = solve_finish(c);
         if (st < 0) return fail(st, nullptr);
         if (st != HPR_OK) worst = st;

@@ -398,6 +398,8 @@ int solve_finish(hpr_ctx *ctx)
     I.iters_fp32 = S.iters_fp32;
     I.policy_decisions = S.policy_decisions;
     I.policy_fallbacks = S.policy_fallbacks;
+    I.path = ctx->path_used;
+    I.path_ctas = ctx->grid_ctas_used;
     ctx->solved = true;
     return S.status;
 }
@@ -408,8 +410,13 @@ constexpr size_t SMALL_SMEM_MAX = 200 * 1024;
 // ~17 cycles each.  Measured on the tiny planted LP, QAPs (N = 5, 6) and medium planted LPs
 // at 1/1000 .. 1/200 scale, an iteration of the single CTA costs ~1.5 us + 8.4 ns per such
 // instruction, and the multi-CTA graph path ~5 us (launch-bound) or more; the default takes
-// the single CTA up to 600 instructions (~6.5 us).
+// the single CTA up to 600 instructions (~6.5 us) against the multi-CTA path, and up to 250
+// (~4 us) when the persistent cluster path can run the LP: one CTA of a cluster issues only
+// its share of the FP64 work, and the cluster's iterations cost ~3.7 us and up (measured on
+// the medium planted LP at 1/1000 scale, 587 instructions: 7.4 us in one CTA, 4.2 us in a
+// cluster of 4).
 constexpr double SMALL_FP64_MAX = 600.0;
+constexpr double SMALL_FP64_VS_CLUSTER = 250.0;
 
 double small_fp64_per_iter(const hpr_ctx *ctx)
 {
@@ -539,6 +546,7 @@ int solve_small(hpr_ctx *ctx, double tol)
     cudaError_t e = cudaMemcpyAsync(ctx->small_args, &A, sizeof A, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = small_launch(ctx->small_args, 1, smem, ctx->stream);
     if (e != cudaSuccess) return fail_cuda(ctx, e, "solve_small", __LINE__);
+    ctx->path_used = 2;
     return small_collect(ctx);
 }
 
@@ -551,6 +559,18 @@ constexpr double GRID_FP64_PER_CTA = 100.0;
 constexpr double GRID_FP64_MAX = 0.0;
 constexpr uint64_t GRID_BUDGET_NS = 5000000000ull;       // 5 s: longest wait at a barrier
 constexpr uint64_t GRID_FAULT_BUDGET_NS = 200000ull;     // 200 us when a skip is injected
+constexpr int CLUSTER_MAX_CTAS = 16;                     // the largest (non-portable) cluster
+// cluster path: CTAs from the FP64 work of an iteration (about CLUSTER_FP64_PER_CTA warp
+// instructions per CTA, 2 to 16), and the largest work it takes by default, counted as the
+// FP64 warp instructions of an iteration plus a quarter of the rows (each row's result is
+// stored into every CTA's replica).  Measured per iteration against the multi-CTA graph path
+// (3,000 iterations): medium planted LPs at 1/1000 .. 1/100 scale 4.2 / 4.8 / 5.0 / 7.3 us
+// against 7.6 / 7.8 / 8.4 / 8.4 (work 760 .. 7,150), QAP N = 8 4.9 against 6.7 (4,450),
+// N = 9 6.0 against 6.0 (7,000); slower above: the medium LP at 1/80 scale 8.5 against 9.0
+// (8,900: about even), the multicommodity-flow LP with 300 nodes 7.4 against 6.4 (8,400),
+// QAP N = 10 8.7 against 7.0 (10,600).
+constexpr double CLUSTER_FP64_PER_CTA = 150.0;
+constexpr double CLUSTER_WORK_MAX = 7500.0;
 
 const char *grid_unfit(const hpr_ctx *ctx, bool forced)
 {
@@ -563,22 +583,16 @@ const char *grid_unfit(const hpr_ctx *ctx, bool forced)
     return nullptr;
 }
 
-int solve_grid(hpr_ctx *ctx, double tol)
+// CTA partial sums of the grid and cluster paths (one buffer serves both)
+int64_t grid_partials_len(const hpr_ctx *ctx)
+{
+    return (int64_t)hprgrid::NQG * std::max(CLUSTER_MAX_CTAS, ctx->num_sms);
+}
+
+// the launch arguments of a persistent grid or cluster solve over G CTAs (A from small_prepare)
+hprgrid::GridArgs grid_args(hpr_ctx *ctx, const hprsmall::SmallArgs &A, int G)
 {
     using namespace hprgrid;
-    hprsmall::SmallArgs A;
-    size_t smem = 0;
-    int st = small_prepare(ctx, tol, A, &smem);   // solve state, record and result buffers
-    if (st) return st;
-    int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_grid, NT, 0));
-    if (per_sm < 1) return fail_arg(ctx, HPR_ERR_CUDA, "the persistent grid kernel does not fit on an SM");
-    const int maxG = std::max(1, ctx->num_sms);
-    int G = (int)std::ceil(small_fp64_per_iter(ctx) / GRID_FP64_PER_CTA);
-    if (ctx->grid_ctas_env > 0) G = (int)std::min<int64_t>(ctx->grid_ctas_env, maxG);
-    G = std::max(2, std::min(G, maxG));
-    if (!ctx->grid_partials) DALLOC(ctx->grid_partials, (int64_t)NQG * maxG);
-    if (!ctx->grid_bar) DALLOC(ctx->grid_bar, 1);
     GridArgs P{};
     P.m = A.m; P.n = A.n; P.G = G;
     P.A = A.A; P.T = A.T;
@@ -599,6 +613,136 @@ int solve_grid(hpr_ctx *ctx, double tol)
     P.skip_cta = ctx->fault_barrier > 0 ? G - 1 : -1;
     P.skip_at = ctx->fault_barrier > 0 ? (int)(ctx->fault_barrier - 1) : -1;
     P.recs = A.recs; P.rec_cap = A.rec_cap; P.out = A.out;
+    return P;
+}
+
+// the largest per-CTA share of the two sliced-ELL matrices for a cluster of G CTAs, from
+// host copies of the slice pointers
+int cluster_dims(hpr_ctx *ctx, int G, hprgrid::ClusterDims *out)
+{
+    using namespace hprgrid;
+    hprgrid::ClusterDims d{};
+    for (int which = 0; which < 2; ++which) {
+        const SellDev &M = which ? ctx->SA : ctx->ST;
+        std::vector<int> srow((size_t)M.nslices + 1), sptr((size_t)M.nslices + 1);
+        CK(cudaMemcpy(srow.data(), M.srow, sizeof(int) * srow.size(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(sptr.data(), M.sptr, sizeof(int) * sptr.size(), cudaMemcpyDeviceToHost));
+        std::vector<int64_t> ent(G, 0), rows(G, 0), nsl(G, 0);
+        for (int sl = 0; sl < M.nslices; ++sl) {
+            const int cta = (sl % (G * NW)) % G;   // warp g = warp * G + CTA owns slices g (mod G * NW)
+            ent[cta] += sptr[sl + 1] - sptr[sl];
+            rows[cta] += srow[sl + 1] - srow[sl];
+            nsl[cta] += 1;
+        }
+        const int e = (int)*std::max_element(ent.begin(), ent.end());
+        const int r = (int)*std::max_element(rows.begin(), rows.end());
+        const int q = (int)*std::max_element(nsl.begin(), nsl.end());
+        if (which) { d.entA = e; d.rowsA = r; d.nslA = q; }
+        else { d.entT = e; d.rowsT = r; d.nslT = q; }
+    }
+    *out = d;
+    return HPR_OK;
+}
+
+// the cluster size of a solve: from the FP64 work of an iteration, or HPR_GRID_CTAS
+int cluster_ctas(const hpr_ctx *ctx)
+{
+    int G = (int)std::ceil(small_fp64_per_iter(ctx) / CLUSTER_FP64_PER_CTA);
+    if (ctx->grid_ctas_env > 0) G = (int)std::min<int64_t>(ctx->grid_ctas_env, CLUSTER_MAX_CTAS);
+    return std::max(2, std::min(G, CLUSTER_MAX_CTAS));
+}
+
+// the shared memory one CTA may have (opt-in limit less the kernel's static shared memory)
+size_t cluster_smem_limit(const hpr_ctx *ctx)
+{
+    cudaFuncAttributes fa{};
+    int optin = 0;
+    if (cudaFuncGetAttributes(&fa, hprgrid::k_solve_cluster) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+}
+
+// whether the persistent cluster path can run this solve (and why not); unless forced, also
+// whether it is expected to be the faster path
+const char *cluster_unfit(hpr_ctx *ctx, bool forced)
+{
+    if (const char *why = grid_unfit(ctx, true)) return why;
+    if (!forced && small_fp64_per_iter(ctx) + 0.25 * (double)(ctx->m + ctx->n) > CLUSTER_WORK_MAX)
+        return "enough work per iteration to fill the GPU from launches";
+    const size_t limit = cluster_smem_limit(ctx);
+    const int G = cluster_ctas(ctx);
+    // a lower bound first (replicas and an even share of the matrices), then the exact need
+    const size_t lower = 8ull * (size_t)(ctx->m + ctx->n) + 12ull * (size_t)(ctx->SA.entries + ctx->ST.entries) / G;
+    hprgrid::ClusterDims d{};
+    if (lower > limit || cluster_dims(ctx, G, &d) != HPR_OK ||
+        hprgrid::cluster_smem_bytes((int)ctx->m, (int)ctx->n, d) > limit)
+        return "the LP does not fit in the shared memory of the cluster";
+    return nullptr;
+}
+
+int solve_cluster(hpr_ctx *ctx, double tol)
+{
+    using namespace hprgrid;
+    hprsmall::SmallArgs A;
+    size_t smem_small = 0;
+    int st = small_prepare(ctx, tol, A, &smem_small);   // solve state, record and result buffers
+    if (st) return st;
+    CK(cudaFuncSetAttribute(k_solve_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    const size_t limit = cluster_smem_limit(ctx);
+    CK(cudaFuncSetAttribute(k_solve_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    cfg.blockDim = dim3(NT);
+    cfg.stream = ctx->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ClusterDims d{};
+    int G = cluster_ctas(ctx);
+    for (; G >= 2; --G) {                    // the largest resident cluster up to G that fits
+        if ((st = cluster_dims(ctx, G, &d))) return st;
+        const size_t smem = cluster_smem_bytes((int)ctx->m, (int)ctx->n, d);
+        if (smem > limit) break;             // fewer CTAs only take larger shares
+        cfg.gridDim = dim3(G);
+        cfg.dynamicSmemBytes = smem;
+        at[0].val.clusterDim.x = (unsigned)G;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, k_solve_cluster, &cfg) == cudaSuccess && nc >= 1) break;
+        (void)cudaGetLastError();
+    }
+    if (G < 2 || cfg.dynamicSmemBytes == 0 || cluster_smem_bytes((int)ctx->m, (int)ctx->n, d) > limit)
+        return fail_arg(ctx, HPR_ERR_ARG, "persistent cluster path: no cluster of two or more CTAs holds the LP");
+    if (!ctx->grid_partials) DALLOC(ctx->grid_partials, grid_partials_len(ctx));
+    GridArgs P = grid_args(ctx, A, G);
+    CK(cudaLaunchKernelEx(&cfg, k_solve_cluster, P, d));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->grid_ctas_used = G;
+    ctx->path_used = 4;
+    return small_collect(ctx);
+}
+
+int solve_grid(hpr_ctx *ctx, double tol)
+{
+    using namespace hprgrid;
+    hprsmall::SmallArgs A;
+    size_t smem = 0;
+    int st = small_prepare(ctx, tol, A, &smem);   // solve state, record and result buffers
+    if (st) return st;
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_grid, NT, 0));
+    if (per_sm < 1) return fail_arg(ctx, HPR_ERR_CUDA, "the persistent grid kernel does not fit on an SM");
+    const int maxG = std::max(1, ctx->num_sms);
+    int G = (int)std::ceil(small_fp64_per_iter(ctx) / GRID_FP64_PER_CTA);
+    if (ctx->grid_ctas_env > 0) G = (int)std::min<int64_t>(ctx->grid_ctas_env, maxG);
+    G = std::max(2, std::min(G, maxG));
+    if (!ctx->grid_partials) DALLOC(ctx->grid_partials, grid_partials_len(ctx));
+    if (!ctx->grid_bar) DALLOC(ctx->grid_bar, 1);
+    GridArgs P = grid_args(ctx, A, G);
     CK(cudaMemsetAsync(ctx->grid_bar, 0, sizeof(GridBar), ctx->stream));
     void *kargs[] = {&P};
     CK(cudaLaunchCooperativeKernel((const void *)k_solve_grid, dim3(G), dim3(NT), kargs, 0, ctx->stream));
@@ -606,6 +750,7 @@ int solve_grid(hpr_ctx *ctx, double tol)
     CK(cudaMemcpyAsync(&hb, ctx->grid_bar, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->grid_ctas_used = G;
+    ctx->path_used = 3;
     if (hb.err)
         return fail_arg(ctx, HPR_ERR_DEVICE_TIMEOUT,
                         "persistent grid solve: a wait at grid barrier " + std::to_string(hb.where) +
@@ -624,11 +769,21 @@ int hpr_solve(hpr_ctx *ctx, double tol)
     if (ctx->batched) return fail_arg(ctx, HPR_ERR_STATE, "the context belongs to a batch");
     cudaSetDevice(ctx->device);
     ctx->grid_ctas_used = 0;
+    ctx->path_used = 0;
     if (ctx->opt.persistent == 1 || ctx->opt.persistent == 2) {
         const char *why = small_unfit(ctx, ctx->opt.persistent == 2);
+        if (!why && ctx->opt.persistent == 1 && small_fp64_per_iter(ctx) > SMALL_FP64_VS_CLUSTER &&
+            !cluster_unfit(ctx, false))
+            why = "the persistent cluster path is faster";
         if (!why) return solve_small(ctx, tol);
         if (ctx->opt.persistent == 2)
             return fail_arg(ctx, HPR_ERR_ARG, std::string("persistent = 2 but the single-CTA path cannot run: ") + why);
+    }
+    if (ctx->opt.persistent == 1 || ctx->opt.persistent == 4) {
+        const char *why = cluster_unfit(ctx, ctx->opt.persistent == 4);
+        if (!why) return solve_cluster(ctx, tol);
+        if (ctx->opt.persistent == 4)
+            return fail_arg(ctx, HPR_ERR_ARG, std::string("persistent = 4 but the persistent cluster path cannot run: ") + why);
     }
     if (ctx->opt.persistent == 1 || ctx->opt.persistent == 3) {
         const char *why = grid_unfit(ctx, ctx->opt.persistent == 3);

@@ -55,6 +55,7 @@ enum {
     Q_W2 = 11,   // power method: ||A A^T u||^2
     Q_V2 = 12,   // generic vector norm (start vector, b, c)
     Q_V2B = 13,
+    Q_POWG = 14, // power method: group sums of the CTA partials
     NQ = 16
 };
 
@@ -762,28 +763,6 @@ struct EpiPrimal {
     }
 };
 
-// power method: out = M xin and the partial ||out||^2
-struct EpiNorm {
-    using Val = double;
-    using Sum = double;
-    static constexpr int NV = 1, NP = 1;
-    const double *xa, *xb;
-    int q[1];
-    double *partials;
-    int pstride;
-    double *out;
-    struct Pre { int unused; };
-    __device__ __forceinline__ void load() {}
-    __device__ __forceinline__ Pre prefetch(int) const { return Pre{0}; }
-    __device__ __forceinline__ void row(int j, bool act, const double *s, const Pre &, double *part) const
-    {
-        if (act) {
-            out[j] = s[0];
-            part[0] = fma(s[0], s[0], part[0]);
-        }
-    }
-};
-
 // power method on A A^* (Section 4.1), two launches a step.  Step k: s = inv * A^T w (w is
 // the previous step's A s, or the start vector, and inv its reciprocal norm, so the
 // normalisation u = w / ||w|| rides in the row sums) with lambda_k = ||s||^2; then w = A s
@@ -860,8 +839,14 @@ struct EpiPowA {
     }
 };
 
-// A power-method launch: the phase kernel's row sums, then the last CTA to finish (a
-// ticket counter, reset by that CTA) sums the CTA partials in CTA order and calls finish.
+// A power-method launch: the phase kernel's row sums, then the CTA partial sums added in a
+// fixed order, in two levels so that no CTA adds more than POW_GROUP of them: the last CTA
+// of each group of POW_GROUP CTAs to finish adds its group's partials in CTA order, and the
+// last group to finish adds the group sums in group order and calls finish.  ticket[0]
+// counts the finished groups and ticket[1 + g] the finished CTAs of group g; the CTA that
+// completes a counter resets it.
+constexpr int POW_GROUP = 256;
+
 template <class E>
 __global__ void __launch_bounds__(SELL_TB, SELL_CTAS_PER_SM) k_sell_pow(SellArgs S, E e, unsigned *ticket)
 {
@@ -874,16 +859,32 @@ __global__ void __launch_bounds__(SELL_TB, SELL_CTAS_PER_SM) k_sell_pow(SellArgs
     double part[1] = {0.0};
     sell_unit(S, ee, run, part);
     const double t = block_sum<SELL_TB>(part[0], red);
+    const int G = (int)gridDim.x, grp = (int)blockIdx.x / POW_GROUP, ngrp = (G + POW_GROUP - 1) / POW_GROUP;
+    const int g0 = grp * POW_GROUP, gsize = min(POW_GROUP, G - g0);
+    double *const P = ee.partials + ee.q[0] * ee.pstride;
+    double *const PG = ee.partials + Q_POWG * ee.pstride;
     if (threadIdx.x == 0) {
-        ee.partials[ee.q[0] * ee.pstride + blockIdx.x] = t;
+        P[blockIdx.x] = t;
         __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        last = atomicAdd(ticket + 1 + grp, 1u) == (unsigned)gsize - 1u;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     double sum = 0.0;
-    for (int g = threadIdx.x; g < (int)gridDim.x; g += SELL_TB) sum += __ldcg(ee.partials + ee.q[0] * ee.pstride + g);
+    for (int g = threadIdx.x; g < gsize; g += SELL_TB) sum += __ldcg(P + g0 + g);
+    sum = block_sum<SELL_TB>(sum, red);
+    if (threadIdx.x == 0) {
+        ticket[1 + grp] = 0u;
+        PG[grp] = sum;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == (unsigned)ngrp - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    sum = 0.0;
+    for (int g = threadIdx.x; g < ngrp; g += SELL_TB) sum += __ldcg(PG + g);
     sum = block_sum<SELL_TB>(sum, red);
     if (threadIdx.x == 0) {
         ee.finish(sum);

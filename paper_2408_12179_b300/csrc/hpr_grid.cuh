@@ -15,8 +15,11 @@
 // HPR_ERR_DEVICE_TIMEOUT.  (A cooperative launch guarantees that all G CTAs are resident,
 // so a healthy run never waits long.)
 //
-// Work split: warp g of the grid (g = CTA * NW + warp) takes slices g, g + G*NW, ... of the
-// same sliced-ELL layouts the multi-CTA path uses, for the whole solve.  Every vector that
+// Work split: warp g of the grid takes slices g, g + G*NW, ... of the same sliced-ELL
+// layouts the multi-CTA path uses, for the whole solve, with the warps numbered CTA-minor
+// (g = warp * G + CTA): consecutive slices go to different CTAs, so the longest slices
+// (rows are numbered by decreasing length) spread over all CTAs instead of all landing in
+// the first one.  Every vector that
 // this launch writes is written and read through L2 (st/ld.global.cg), never through a
 // possibly stale L1 line of another SM; the matrices and the LP data are read-only.
 //
@@ -200,11 +203,126 @@ __device__ __forceinline__ void grid_sums_then(const double *partials, int G, Gf
     if (lane == 0) g(static_cast<const double *>(sum));
 }
 
+// Algorithm 2's outer-loop state: thread 0 of every CTA keeps its own copy, and all copies
+// stay equal because every CTA sees bitwise the same check sums
+struct OuterState {
+    int64_t r = 0, nrec = 0, i1e4 = -1;
+    double R0 = 0.0, Rprev = 0.0, t1e4 = -1.0;
+    double pobj = 0, dobj = 0, errp = 0, errd = 0, gap = 0, kkt = 0;
+    int status = 1;                                    // HPR_MAX_ITER
+};
+
+// The decisions at a check from its grid sums (thread 0 of a CTA): the merit R~ of eq.
+// (def:M), the termination test of Section 4.1, the restart criteria eq. (restart_1)-
+// (restart_3) and Algorithm 3's sigma.  CTA 0 writes the check record.  Returns in
+// *restart / *stop whether the inner loop restarts / the solve ends, and the next sigma.
+__device__ __forceinline__ void check_decide(const GridArgs &P, OuterState &D, const double *sums, int64_t k,
+                                             int64_t t_all, bool is_r0, bool is_check, double sigma,
+                                             double lambda, double elapsed, int *restart, int *stop,
+                                             double *sigma_out)
+{
+    const double S_DX2 = sums[0], S_XX0 = sums[1], S_CX = sums[2], S_BND = sums[3], S_DY2 = sums[4];
+    const double S_YY0 = sums[5], S_BY = sums[6], S_RD = sums[7], S_RP = sums[8], S_CROSS = sums[9];
+    // ||w - w_hat||_M = 2 ||w - w_bar||_M, eq. (def:M) with T1 = lambda I - A A^*
+    const double qm = sigma * lambda * S_DY2 + 2.0 * S_CROSS + S_DX2 / sigma;
+    const double Rt = 2.0 * sqrt(qm > 0.0 ? qm : 0.0);
+    const bool rec_ok = blockIdx.x == 0 && D.nrec < P.rec_cap;
+    *restart = 0;
+    *stop = 0;
+    *sigma_out = sigma;
+    if (is_r0 && !is_check) {
+        D.R0 = Rt;
+        D.Rprev = Rt;
+        if (rec_ok) {
+            hpr_check_record rec{};
+            rec.k = k; rec.r = D.r; rec.t = 0; rec.kind = 2; rec.cause = 0;
+            rec.sigma = sigma; rec.Rt = D.R0; rec.R0 = D.R0; rec.sigma_next = sigma;
+            rec.elapsed_s = elapsed; rec.action = -1; rec.sigma_rule = sigma;
+            P.recs[D.nrec] = rec;
+        }
+        ++D.nrec;
+        return;
+    }
+    if (is_r0) {
+        D.R0 = Rt;
+        D.Rprev = Rt;
+    }
+    // termination test of Section 4.1 in the original space
+    const double bb = P.beta_b * P.beta_c;
+    D.errp = sqrt(S_RP) / (1.0 + P.norm_b);
+    D.errd = sqrt(S_RD) / (1.0 + P.norm_c);
+    D.pobj = bb * S_CX;
+    D.dobj = bb * (S_BY + S_BND);
+    D.gap = fabs(D.dobj - D.pobj) / (1.0 + fabs(D.pobj) + fabs(D.dobj));
+    D.kkt = fmax(D.errp, fmax(D.errd, D.gap));
+    if (D.t1e4 < 0.0 && D.kkt <= 1e-4) {
+        D.t1e4 = elapsed;
+        D.i1e4 = k + 1;
+    }
+    int cause = 0;
+    double sigma_next = sigma, Dx = 0.0, Dy = 0.0;
+    if (!(D.kkt == D.kkt) || !(Rt == Rt) || isinf(D.kkt) || isinf(Rt)) {
+        D.status = -6;                                 // HPR_ERR_NUMERIC
+        *stop = 1;
+    } else if (D.kkt <= P.tol) {
+        D.status = 0;
+        cause = -1;
+        *stop = 1;
+    } else if (k + 1 < P.max_iter && P.restart && !is_r0) {
+        // restart criteria eq. (restart_1)-(restart_3)
+        if (Rt <= P.alpha1 * D.R0) cause = 1;
+        else if (Rt <= P.alpha2 * D.R0 && Rt > D.Rprev) cause = 2;
+        else if ((double)(t_all + 1) >= P.alpha3 * (double)(k + 1)) cause = 3;
+        D.Rprev = Rt;
+        *restart = cause != 0;
+    }
+    if (*restart) {
+        // Algorithm 3 with eq. (sigma_T1!=0)
+        Dx = sqrt(S_XX0);
+        Dy = sqrt(lambda) * sqrt(S_YY0);
+        const double ratio = D.errd / D.errp;
+        if (P.sigma_update && Dx > 1e-16 && Dx < 1e12 && Dy > 1e-16 && Dy < 1e12 && D.errp > 0.0 &&
+            ratio > 1e-8 && ratio < 1e8)
+            sigma_next = Dx / Dy;
+        else
+            sigma_next = P.sigma_update ? 1.0 : sigma;
+    }
+    if (rec_ok) {
+        hpr_check_record rec{};
+        rec.k = k; rec.r = D.r; rec.t = t_all; rec.kind = 1 + (is_r0 ? 2 : 0); rec.cause = cause;
+        rec.sigma = sigma; rec.err_p = D.errp; rec.err_d = D.errd; rec.err_gap = D.gap; rec.kkt = D.kkt;
+        rec.pobj = D.pobj; rec.dobj = D.dobj; rec.Rt = Rt; rec.R0 = D.R0; rec.sigma_next = sigma_next;
+        rec.Dx = Dx; rec.Dy = Dy; rec.elapsed_s = elapsed; rec.action = -1; rec.sigma_rule = sigma_next;
+        P.recs[D.nrec] = rec;
+    }
+    ++D.nrec;
+    if (*restart) {
+        *sigma_out = sigma_next;
+        ++D.r;
+    }
+}
+
+// the results of a persistent solve (CTA 0, thread 0)
+__device__ __forceinline__ void write_out(const GridArgs &P, const OuterState &D, int64_t k, double lambda,
+                                          int64_t piters, double sigma, double prel, uint64_t t_start,
+                                          uint64_t t_power)
+{
+    double *o = P.out;
+    using namespace hprsmall;
+    o[SO_ITERS] = (double)k; o[SO_RESTARTS] = (double)D.r; o[SO_STATUS] = (double)D.status;
+    o[SO_LAMBDA] = lambda; o[SO_POWER_ITERS] = (double)piters; o[SO_SIGMA] = sigma;
+    o[SO_POBJ] = D.pobj; o[SO_DOBJ] = D.dobj; o[SO_ERRP] = D.errp; o[SO_ERRD] = D.errd; o[SO_GAP] = D.gap;
+    o[SO_KKT] = D.kkt; o[SO_T1E4] = D.t1e4; o[SO_I1E4] = (double)D.i1e4; o[SO_NREC] = (double)D.nrec;
+    o[SO_POWER_S] = 1e-9 * (double)(t_power - t_start);
+    o[SO_TOTAL_S] = 1e-9 * (double)(hprsmall::now_ns() - t_start);
+    o[SO_POWER_REL] = prel;
+}
+
 __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
 {
     using hprsmall::now_ns;
     const int tid = threadIdx.x, G = P.G;
-    const int gw = blockIdx.x * NW + (tid >> 5), GW = G * NW;
+    const int gw = (tid >> 5) * G + blockIdx.x, GW = G * NW;   // CTA-minor warp numbering
     const hprsmall::SmallMat MA = P.A, MT = P.T;
     const int n = P.n, m = P.m;
     double *x = P.x, *x0 = P.x0, *xh = P.xh, *xb = P.xb, *zb = P.zb, *dx = P.dx;
@@ -302,10 +420,8 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
         __stcg(y0 + i, 0.0);
     }
     if (!grid_sync(P, nb++, &s_ok)) return;
-    int64_t k = 0, r = 0, nrec = 0, i1e4 = -1;
-    double R0 = 0.0, Rprev = 0.0, t1e4 = -1.0;
-    double pobj = 0, dobj = 0, errp = 0, errd = 0, gap = 0, kkt = 0;
-    int status = 1;                                    // HPR_MAX_ITER
+    int64_t k = 0;
+    OuterState D;
     int64_t t_all = 0;
     int64_t to_check = P.check_every;
     int fresh = 0;                                     // 1: first iteration after a restart
@@ -397,86 +513,14 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
         cta_publish<NQG>(q, red, P.partials, G);
         if (!grid_sync(P, nb++, &s_ok)) return;
         grid_sums_then<NQG>(P.partials, G, [&](const double *sums) {
-            const double S_DX2 = sums[0], S_XX0 = sums[1], S_CX = sums[2], S_BND = sums[3], S_DY2 = sums[4];
-            const double S_YY0 = sums[5], S_BY = sums[6], S_RD = sums[7], S_RP = sums[8], S_CROSS = sums[9];
-            // ||w - w_hat||_M = 2 ||w - w_bar||_M, eq. (def:M) with T1 = lambda I - A A^*
-            const double qm = sigma * lambda * S_DY2 + 2.0 * S_CROSS + S_DX2 / sigma;
-            const double Rt = 2.0 * sqrt(qm > 0.0 ? qm : 0.0);
-            const double elapsed = 1e-9 * (double)(now_ns() - t_start);
-            const bool rec_ok = blockIdx.x == 0 && nrec < P.rec_cap;
-            bc_restart = 0;
-            bc_stop = 0;
-            if (is_r0 && !is_check) {
-                R0 = Rt;
-                Rprev = Rt;
-                if (rec_ok) {
-                    hpr_check_record rec{};
-                    rec.k = k; rec.r = r; rec.t = 0; rec.kind = 2; rec.cause = 0;
-                    rec.sigma = sigma; rec.Rt = R0; rec.R0 = R0; rec.sigma_next = sigma;
-                    rec.elapsed_s = elapsed; rec.action = -1; rec.sigma_rule = sigma;
-                    P.recs[nrec] = rec;
-                }
-                ++nrec;
-            } else {
-                if (is_r0) {
-                    R0 = Rt;
-                    Rprev = Rt;
-                }
-                // termination test of Section 4.1 in the original space
-                const double bb = P.beta_b * P.beta_c;
-                errp = sqrt(S_RP) / (1.0 + P.norm_b);
-                errd = sqrt(S_RD) / (1.0 + P.norm_c);
-                pobj = bb * S_CX;
-                dobj = bb * (S_BY + S_BND);
-                gap = fabs(dobj - pobj) / (1.0 + fabs(pobj) + fabs(dobj));
-                kkt = fmax(errp, fmax(errd, gap));
-                if (t1e4 < 0.0 && kkt <= 1e-4) {
-                    t1e4 = elapsed;
-                    i1e4 = k + 1;
-                }
-                int cause = 0;
-                double sigma_next = sigma, Dx = 0.0, Dy = 0.0;
-                if (!(kkt == kkt) || !(Rt == Rt) || isinf(kkt) || isinf(Rt)) {
-                    status = -6;                       // HPR_ERR_NUMERIC
-                    bc_stop = 1;
-                } else if (kkt <= P.tol) {
-                    status = 0;
-                    cause = -1;
-                    bc_stop = 1;
-                } else if (k + 1 < P.max_iter && P.restart && !is_r0) {
-                    // restart criteria eq. (restart_1)-(restart_3)
-                    if (Rt <= P.alpha1 * R0) cause = 1;
-                    else if (Rt <= P.alpha2 * R0 && Rt > Rprev) cause = 2;
-                    else if ((double)(t_all + 1) >= P.alpha3 * (double)(k + 1)) cause = 3;
-                    Rprev = Rt;
-                    bc_restart = cause != 0;
-                }
-                if (bc_restart) {
-                    // Algorithm 3 with eq. (sigma_T1!=0)
-                    Dx = sqrt(S_XX0);
-                    Dy = sqrt(lambda) * sqrt(S_YY0);
-                    const double ratio = errd / errp;
-                    if (P.sigma_update && Dx > 1e-16 && Dx < 1e12 && Dy > 1e-16 && Dy < 1e12 && errp > 0.0 &&
-                        ratio > 1e-8 && ratio < 1e8)
-                        sigma_next = Dx / Dy;
-                    else
-                        sigma_next = P.sigma_update ? 1.0 : sigma;
-                }
-                if (rec_ok) {
-                    hpr_check_record rec{};
-                    rec.k = k; rec.r = r; rec.t = t_all; rec.kind = 1 + (is_r0 ? 2 : 0); rec.cause = cause;
-                    rec.sigma = sigma; rec.err_p = errp; rec.err_d = errd; rec.err_gap = gap; rec.kkt = kkt;
-                    rec.pobj = pobj; rec.dobj = dobj; rec.Rt = Rt; rec.R0 = R0; rec.sigma_next = sigma_next;
-                    rec.Dx = Dx; rec.Dy = Dy; rec.elapsed_s = elapsed; rec.action = -1; rec.sigma_rule = sigma_next;
-                    P.recs[nrec] = rec;
-                }
-                ++nrec;
-                if (bc_restart) {
-                    set_sigma(sigma_next);
-                    ++r;
-                }
-            }
-            set_weights(bc_restart ? 0 : t_all + 1);
+            int rs, stp;
+            double sn;
+            check_decide(P, D, sums, k, t_all, is_r0, is_check, sigma, lambda, 1e-9 * (double)(now_ns() - t_start),
+                         &rs, &stp, &sn);
+            bc_restart = rs;
+            bc_stop = stp;
+            if (rs) set_sigma(sn);
+            set_weights(rs ? 0 : t_all + 1);
         });
         __syncthreads();
         if (bc_stop) {
@@ -490,17 +534,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
             ++t_all;
         }
     }
-    if (blockIdx.x == 0 && tid == 0) {
-        double *o = P.out;
-        using namespace hprsmall;
-        o[SO_ITERS] = (double)k; o[SO_RESTARTS] = (double)r; o[SO_STATUS] = (double)status;
-        o[SO_LAMBDA] = lambda; o[SO_POWER_ITERS] = (double)piters; o[SO_SIGMA] = bc_sigma;
-        o[SO_POBJ] = pobj; o[SO_DOBJ] = dobj; o[SO_ERRP] = errp; o[SO_ERRD] = errd; o[SO_GAP] = gap;
-        o[SO_KKT] = kkt; o[SO_T1E4] = t1e4; o[SO_I1E4] = (double)i1e4; o[SO_NREC] = (double)nrec;
-        o[SO_POWER_S] = 1e-9 * (double)(t_power - t_start);
-        o[SO_TOTAL_S] = 1e-9 * (double)(now_ns() - t_start);
-        o[SO_POWER_REL] = prel;
-    }
+    if (blockIdx.x == 0 && tid == 0) write_out(P, D, k, lambda, piters, bc_sigma, prel, t_start, t_power);
 }
 
 }  // namespace hprgrid

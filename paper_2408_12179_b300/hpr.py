@@ -64,7 +64,7 @@ class hpr_info(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("status", ctypes.c_int64),
                 ("iters_fp32", ctypes.c_int64),
                 ("policy_decisions", ctypes.c_int64), ("policy_fallbacks", ctypes.c_int64),
-                ("power_rel_change", ctypes.c_double)]
+                ("power_rel_change", ctypes.c_double), ("path", ctypes.c_int64), ("path_ctas", ctypes.c_int64)]
 
 
 class hpr_check_record(ctypes.Structure):

@@ -94,18 +94,23 @@ def test_persistent_is_faster_per_iteration():
 
 
 def test_default_path_choice():
-    """persistent = 1 takes the single CTA for the tiny planted LP and the multi-CTA path for a
-    medium planted LP at 1/200 scale, whose iterates fit in shared memory but whose FP64 work
-    per iteration is beyond what one SM does faster; persistent = 2 still runs it in one CTA,
-    to the same result as the multi-CTA path."""
-    lp = lpgen.planted_medium(0, 0.005)
+    """persistent = 1 takes the single CTA for the tiny planted LP, the persistent cluster path
+    for a medium planted LP at 1/200 scale (its FP64 work per iteration is beyond what one SM
+    does faster, and it fits in the cluster's shared memory) and the multi-CTA path at 1/20
+    scale (it does not fit); persistent = 2 still runs the 1/200 LP in one CTA, to the same
+    iterates' quality (hpr_info.path names the path taken)."""
     with hpr.Solver(lpgen.planted_tiny(0), persistent=1) as s:
-        assert s.solve(1e-8)["info"]["launches"] <= 3
+        I = s.solve(1e-8)["info"]
+        assert I["launches"] <= 3 and I["path"] == 2 and I["path_ctas"] == 0
+    lp = lpgen.planted_medium(0, 0.005)
     res = {}
-    for p in (1, 2):
+    for p, path in ((1, 4), (2, 2), (0, 0)):
         with hpr.Solver(lp, persistent=p, max_iter=1500) as s:
             r = s.solve(1e-8)
-        assert (r["info"]["launches"] <= 3) == (p == 2)
+        assert r["info"]["path"] == path and (r["info"]["launches"] <= 3) == (path != 0)
+        assert (r["info"]["path_ctas"] > 1) == (path == 4)
         res[p] = r
-    assert res[1]["info"]["iters"] == res[2]["info"]["iters"] == 1500
+    assert res[0]["info"]["iters"] == res[1]["info"]["iters"] == res[2]["info"]["iters"] == 1500
     assert res[2]["info"]["kkt"] == pytest.approx(res[1]["info"]["kkt"], rel=1e-3)
+    with hpr.Solver(lpgen.planted_medium(0, 0.05), persistent=1, max_iter=300) as s:
+        assert s.solve(1e-8)["info"]["path"] == 0
