@@ -154,6 +154,7 @@ struct hpr_ctx {
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::map<GraphKey, int64_t> graph_launches;   // kernel nodes per captured period
     cudaGraphExec_t pow_graph = nullptr;
+    int64_t pow_graph_launches = 0;   // kernels of one launch of pow_graph
 
     // host structure of the layouts that the small-phase rule gave short slices, kept so
     // that a batch whose fused phases move enough data can lay them out for throughput
@@ -818,6 +819,7 @@ int run_power(hpr_ctx *ctx)
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         const int64_t before = ctx->launches;
         int r = enqueue_steps(BATCH);
+        ctx->pow_graph_launches = ctx->launches - before;
         ctx->launches = before;
         cudaGraph_t gg = nullptr;
         cudaError_t e = cudaStreamEndCapture(ctx->stream, &gg);
@@ -831,7 +833,7 @@ int run_power(hpr_ctx *ctx)
     ctx->launches += 2;   // start vector, 1/norm (+1 for the reduction above)
     for (int64_t done_steps = 0; done_steps <= ctx->opt.power_max_iter; done_steps += BATCH) {
         if (ctx->opt.use_graph) {
-            ctx->launches += (int64_t)BATCH * 2;
+            ctx->launches += ctx->pow_graph_launches;
             CK(cudaGraphLaunch(ctx->pow_graph, ctx->stream));
         } else {
             int r = enqueue_steps(BATCH);
