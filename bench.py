@@ -261,7 +261,8 @@ def run_reference(args):
 
 def run_batch(args):
     """Batched workload: `count` uneven planted LPs solved together through hpr_batch_*
-    (fused launches), one context per LP.  Warm-up solves are capped at two check
+    (cluster launches for the LPs whose own solve takes the persistent cluster path, fused
+    launches for the others), one context per LP.  Warm-up solves are capped at two check
     periods (graph capture, power method); the timed solve runs every LP to tol or the
     iteration cap.  Also times a sample of the LPs solved one by one and as a batch of
     their own (same instances, same options)."""
@@ -275,7 +276,7 @@ def run_batch(args):
     m_hi = max(600, int(round(50_000 * args.scale)))
     lps = lpgen.batch_family(args.seed + rank, args.count, 500, m_hi)
     stream = torch.cuda.Stream()
-    opts = dict(tol=args.tol, precision=args.precision, **VARIANTS[args.variant])
+    opts = dict(tol=args.tol, precision=args.precision, persistent=args.persistent, **VARIANTS[args.variant])
     opts.update(layout_opts(args))
     t_create = time.perf_counter()
     if args.autotune:
@@ -355,7 +356,7 @@ def run_batch(args):
         "config": {"workload": f"batch of {len(lps)} uneven planted LPs (m log-uniform in [500, {m_hi}], "
                                f"n = 2.5 m, density log-uniform in [0.1%, 1%], medium-LP value rules; "
                                f"total nnz {nnz}, seed {args.seed})",
-                   "tol": args.tol, "max_iter": args.max_iter, "variant": args.variant,
+                   "tol": args.tol, "max_iter": args.max_iter, "variant": args.variant, "persistent": args.persistent,
                    "autotune": ({str(k): v for k, v in sorted(tuned.items())} if tuned else None),
                    "layout": layout_opts(args) or "library default",
                    "l2": batch_l2,
@@ -363,6 +364,10 @@ def run_batch(args):
         "batch_status": hpr.hpr_status_str(int(status)), "converged": len(conv), "count": len(lps),
         "time_to_all_s": secs, "iters_summed": iters, "iters_per_s_summed": iters / secs,
         "periods": st["periods"], "gpu_launches": int(st["fused_launches"] + sum(int(r["info"]["launches"]) for r in res)),
+        "paths": {name: sum(int(r["info"]["path"]) == code for r in res)
+                  for name, code in (("fused", 0), ("single_cta", 2), ("cluster", 4))},
+        "converged_by_path": {name: sum(int(r["info"]["path"]) == code and r["status"] == hpr.HPR_OK for r in res)
+                              for name, code in (("fused", 0), ("single_cta", 2), ("cluster", 4))},
         "sample": {"lps": k, "one_by_one_s": solo_secs, "as_batch_s": sample_batch_secs,
                    "speedup": solo_secs / sample_batch_secs, "iters": solo_iters},
         "clocks": clocks,
@@ -751,6 +756,8 @@ def parse_args(argv=None):
                     help="batch workload: LPs also solved one by one, and as a batch of their own")
     ap.add_argument("--variant", choices=list(VARIANTS), default="hpr",
                     help="ablation variant of Section 4.2 (default: HPR-LP itself)")
+    ap.add_argument("--persistent", type=int, default=1, choices=[0, 1, 2, 3, 4],
+                    help="batch workload: hpr_options.persistent of every LP (0: the fused path only)")
     ap.add_argument("--lambda-fixed", dest="lambda_fixed", type=float, default=0.0,
                     help="use this lambda instead of the power method (short profiling runs)")
     args = ap.parse_args(argv)

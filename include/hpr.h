@@ -346,6 +346,10 @@ int hpr_layout_plan(const hpr_csr *B, int64_t steps_max, double unit_cost, int64
  * When every context would take the persistent single-CTA path on its own (see
  * hpr_options.persistent), the batch runs them as one launch with one CTA per LP, each
  * result equal to the context's own single-CTA solve (hpr_batch_stats: 0 periods, 1 launch).
+ * Otherwise, when every context would take the persistent cluster path on its own, the
+ * batch runs one launch per cluster size among them, each on a stream of its own, with
+ * one cluster per LP (costliest first), each result equal to the context's own cluster
+ * solve (hpr_batch_stats: 0 periods, one launch per cluster size).
  * hpr_batch_solve returns HPR_OK when every context converged, else the status of a
  * context that did not (HPR_MAX_ITER / HPR_TIME_LIMIT), or an error code; detail in
  * hpr_last_error(NULL) or of the context. */
@@ -353,7 +357,7 @@ typedef struct hpr_batch hpr_batch;
 int hpr_batch_create(hpr_batch **out, int64_t count, hpr_ctx *const *ctxs, void *cuda_stream);
 int hpr_batch_solve(hpr_batch *batch, double tol);
 /* Wall time of the last hpr_batch_solve (power methods included), its check periods and
- * the fused launches it made; any pointer may be NULL. */
+ * the fused (or persistent) launches it made; any pointer may be NULL. */
 int hpr_batch_stats(const hpr_batch *batch, double *solve_time_s, int64_t *periods, int64_t *fused_launches);
 void hpr_batch_destroy(hpr_batch *batch);
 

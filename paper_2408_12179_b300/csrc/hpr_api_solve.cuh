@@ -652,17 +652,20 @@ int cluster_ctas(const hpr_ctx *ctx)
     return std::max(2, std::min(G, CLUSTER_MAX_CTAS));
 }
 
-// the shared memory one CTA may have (opt-in limit less the kernel's static shared memory)
+// the dynamic shared memory one CTA of the cluster kernels may have (the opt-in limit less
+// the larger static shared memory of the solo and the batch kernel)
 size_t cluster_smem_limit(const hpr_ctx *ctx)
 {
-    cudaFuncAttributes fa{};
+    cudaFuncAttributes fa{}, fb{};
     int optin = 0;
     if (cudaFuncGetAttributes(&fa, hprgrid::k_solve_cluster) != cudaSuccess ||
+        cudaFuncGetAttributes(&fb, hprgrid::k_solve_cluster_batch) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) != cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }
-    return (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    const size_t st = std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
+    return (size_t)optin > st ? (size_t)optin - st : 0;
 }
 
 // whether the persistent cluster path can run this solve (and why not); unless forced, also

@@ -177,11 +177,12 @@ __device__ __forceinline__ void cl_own_rows(const SlMeta *meta, int s0, int ns, 
     }
 }
 
-__global__ void __launch_bounds__(NT, 1) k_solve_cluster(GridArgs P, ClusterDims CD)
+// The whole solve of one LP by the CTA of rank `rank` in a cluster of P.G CTAs.
+__device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDims &CD, const int rank)
 {
     using hprsmall::now_ns;
     const int tid = threadIdx.x, G = P.G;
-    const int gw = (tid >> 5) * G + blockIdx.x, GW = G * NW;   // CTA-minor warp numbering
+    const int gw = (tid >> 5) * G + rank, GW = G * NW;   // CTA-minor warp numbering
     const int n = P.n, m = P.m;
     double *xb = P.xb, *zb = P.zb, *dx = P.dx, *yb = P.yb, *dy = P.dy;
     __shared__ double red[NQG * NW];
@@ -239,12 +240,12 @@ __global__ void __launch_bounds__(NT, 1) k_solve_cluster(GridArgs P, ClusterDims
     double prel = 0.0;
     if (!(lambda > 0.0)) {
         double p[1] = {0.0};
-        for (int i = blockIdx.x * NT + tid; i < m; i += G * NT) {
+        for (int i = rank * NT + tid; i < m; i += G * NT) {
             const double v = 2.0 * ((double)(hprdev::splitmix64_at(P.seed, (uint64_t)P.perm_r[i]) >> 11) * 0x1.0p-53) - 1.0;
             bcast(s_peer_y, i, v);
             p[0] = fma(v, v, p[0]);
         }
-        cta_publish<1>(p, red, P.partials, G);
+        cta_publish<1>(p, red, P.partials, G, rank);
         cluster_barrier();
         grid_sums_then<1>(P.partials, G, [&](const double *sum) {
             sc[0] = 1.0 / sqrt(sum[0]);
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(NT, 1) k_solve_cluster(GridArgs P, ClusterDims
                 q[1] = fma(wi, wi, q[1]);
             });
             ++k;
-            cta_publish<2>(q, red, P.partials, G);
+            cta_publish<2>(q, red, P.partials, G, rank);
             cluster_barrier();
             grid_sums_then<2>(P.partials, G, [&](const double *sum) {
                 const double l = sum[0], prev = sc[1];
@@ -381,13 +382,13 @@ __global__ void __launch_bounds__(NT, 1) k_solve_cluster(GridArgs P, ClusterDims
             q[8] = fma(ri, ri, q[8]);
         });
         rowsA([&](int c) { return __ldcg(dx + c); }, [&](int i, int, double si) { q[9] = fma(__ldcg(dy + i), si, q[9]); });
-        cta_publish<NQG>(q, red, P.partials, G);
+        cta_publish<NQG>(q, red, P.partials, G, rank);
         cluster_barrier();
         grid_sums_then<NQG>(P.partials, G, [&](const double *sums) {
             int rs, stp;
             double sn;
-            check_decide(P, D, sums, k, t_all, is_r0, is_check, sigma, lambda, 1e-9 * (double)(now_ns() - t_start),
-                         &rs, &stp, &sn);
+            check_decide(P, D, sums, rank, k, t_all, is_r0, is_check, sigma, lambda,
+                         1e-9 * (double)(now_ns() - t_start), &rs, &stp, &sn);
             bc_restart = rs;
             bc_stop = stp;
             if (rs) set_sigma(sn);
@@ -416,7 +417,31 @@ __global__ void __launch_bounds__(NT, 1) k_solve_cluster(GridArgs P, ClusterDims
         }
     }
     cluster_barrier();                        // no CTA leaves while a peer may still store to it
-    if (blockIdx.x == 0 && tid == 0) write_out(P, D, k, lambda, piters, bc_sigma, prel, t_start, t_power);
+    if (rank == 0 && tid == 0) write_out(P, D, k, lambda, piters, bc_sigma, prel, t_start, t_power);
+}
+
+// one LP: the launch is one cluster (grid = cluster = P.G CTAs)
+__global__ void __launch_bounds__(NT, 1) k_solve_cluster(GridArgs P, ClusterDims CD)
+{
+    cluster_solve(P, CD, (int)blockIdx.x);
+}
+
+// a batch: cluster c of the launch solves jobs[c] (every job's P.G is the launch's cluster
+// size; the dynamic shared memory is the largest job's)
+struct ClusterJob {
+    GridArgs P;
+    ClusterDims CD;
+};
+
+__global__ void __launch_bounds__(NT, 1) k_solve_cluster_batch(const ClusterJob *__restrict__ jobs)
+{
+    __shared__ ClusterJob job;
+    unsigned rank, cid;
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+    if (threadIdx.x == 0) job = jobs[cid];
+    __syncthreads();
+    cluster_solve(job.P, job.CD, (int)rank);
 }
 
 }  // namespace hprgrid

@@ -157,9 +157,10 @@ __device__ __forceinline__ void grid_rows(const hprsmall::SmallMat &M, const dou
 }
 
 // Fixed-order CTA sums of NV values per thread (xor butterfly in each warp, then warp 0 over
-// the NW warp sums in warp order) published as this CTA's partials; red holds NV * NW doubles.
+// the NW warp sums in warp order) published as the partials of CTA `rank` of the launch (or
+// cluster); red holds NV * NW doubles.
 template <int NV>
-__device__ __forceinline__ void cta_publish(double (&v)[NV], double *red, double *partials, int G)
+__device__ __forceinline__ void cta_publish(double (&v)[NV], double *red, double *partials, int G, int rank)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -178,7 +179,7 @@ __device__ __forceinline__ void cta_publish(double (&v)[NV], double *red, double
             double s = lane < NW ? red[q * NW + lane] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) __stcg(partials + q * G + blockIdx.x, s);
+            if (lane == 0) __stcg(partials + q * G + rank, s);
         }
     }
 }
@@ -214,10 +215,10 @@ struct OuterState {
 
 // The decisions at a check from its grid sums (thread 0 of a CTA): the merit R~ of eq.
 // (def:M), the termination test of Section 4.1, the restart criteria eq. (restart_1)-
-// (restart_3) and Algorithm 3's sigma.  CTA 0 writes the check record.  Returns in
+// (restart_3) and Algorithm 3's sigma.  CTA (rank) 0 writes the check record.  Returns in
 // *restart / *stop whether the inner loop restarts / the solve ends, and the next sigma.
-__device__ __forceinline__ void check_decide(const GridArgs &P, OuterState &D, const double *sums, int64_t k,
-                                             int64_t t_all, bool is_r0, bool is_check, double sigma,
+__device__ __forceinline__ void check_decide(const GridArgs &P, OuterState &D, const double *sums, int rank,
+                                             int64_t k, int64_t t_all, bool is_r0, bool is_check, double sigma,
                                              double lambda, double elapsed, int *restart, int *stop,
                                              double *sigma_out)
 {
@@ -226,7 +227,7 @@ __device__ __forceinline__ void check_decide(const GridArgs &P, OuterState &D, c
     // ||w - w_hat||_M = 2 ||w - w_bar||_M, eq. (def:M) with T1 = lambda I - A A^*
     const double qm = sigma * lambda * S_DY2 + 2.0 * S_CROSS + S_DX2 / sigma;
     const double Rt = 2.0 * sqrt(qm > 0.0 ? qm : 0.0);
-    const bool rec_ok = blockIdx.x == 0 && D.nrec < P.rec_cap;
+    const bool rec_ok = rank == 0 && D.nrec < P.rec_cap;
     *restart = 0;
     *stop = 0;
     *sigma_out = sigma;
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
             __stcg(yb + i, v);
             p[0] = fma(v, v, p[0]);
         }
-        cta_publish<1>(p, red, P.partials, G);
+        cta_publish<1>(p, red, P.partials, G, blockIdx.x);
         if (!grid_sync(P, nb++, &s_ok)) return;
         grid_sums_then<1>(P.partials, G, [&](const double *sum) {
             sc[0] = 1.0 / sqrt(sum[0]);
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
                 q[1] = fma(wi, wi, q[1]);
             });
             ++k;
-            cta_publish<2>(q, red, P.partials, G);
+            cta_publish<2>(q, red, P.partials, G, blockIdx.x);
             if (!grid_sync(P, nb++, &s_ok)) return;
             grid_sums_then<2>(P.partials, G, [&](const double *sum) {
                 const double l = sum[0], prev = sc[1];
@@ -510,13 +511,13 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
             q[8] = fma(ri, ri, q[8]);
         });
         grid_rows(MA, dx, gw, GW, [&](int i, double si) { q[9] = fma(__ldcg(dy + i), si, q[9]); });
-        cta_publish<NQG>(q, red, P.partials, G);
+        cta_publish<NQG>(q, red, P.partials, G, blockIdx.x);
         if (!grid_sync(P, nb++, &s_ok)) return;
         grid_sums_then<NQG>(P.partials, G, [&](const double *sums) {
             int rs, stp;
             double sn;
-            check_decide(P, D, sums, k, t_all, is_r0, is_check, sigma, lambda, 1e-9 * (double)(now_ns() - t_start),
-                         &rs, &stp, &sn);
+            check_decide(P, D, sums, blockIdx.x, k, t_all, is_r0, is_check, sigma, lambda,
+                         1e-9 * (double)(now_ns() - t_start), &rs, &stp, &sn);
             bc_restart = rs;
             bc_stop = stp;
             if (rs) set_sigma(sn);

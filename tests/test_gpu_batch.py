@@ -43,7 +43,7 @@ def _solo(lp, **opts):
 def test_batch_equals_solo_solves(precisions):
     lps = _family()
     prec = [0] * len(lps) if precisions == "fp64" else [i % 2 for i in range(len(lps))]
-    solvers = [hpr.Solver(lp, precision=p, max_iter=CAP) for lp, p in zip(lps, prec)]
+    solvers = [hpr.Solver(lp, precision=p, max_iter=CAP, persistent=0) for lp, p in zip(lps, prec)]
     try:
         with hpr.Batch(solvers) as b:
             status, res = b.solve(1e-8)
@@ -124,6 +124,43 @@ def test_large_batch_lays_out_small_contexts_for_throughput():
                 assert np.array_equal(r[key], solo[key]), (lp.name, key)
     finally:
         for s in solvers:
+            s.close()
+
+
+def test_batch_of_cluster_solves():
+    """A batch whose LPs all take the persistent cluster path on their own runs as cluster
+    launches (one per cluster size, one cluster per LP, on streams of their own) with no
+    check period on the host; every result equals the LP's own default solve bit for bit.
+    One LP that does not fit a cluster sends the whole batch to the fused path."""
+    lps = [lpgen.planted_medium(0, 0.001), lpgen.planted_medium(1, 0.002), lpgen.planted_medium(2, 0.005),
+           lpgen.qap_lp(2, 6), lpgen.planted_medium(4, 0.003)]
+    solvers = [hpr.Solver(lp, max_iter=CAP) for lp in lps]
+    try:
+        with hpr.Batch(solvers) as b:
+            status, res = b.solve(1e-8)
+            st = b.stats()
+        assert [int(r["info"]["path"]) for r in res] == [4] * len(lps)
+        sizes = {int(r["info"]["path_ctas"]) for r in res}
+        assert st["periods"] == 0 and st["fused_launches"] == len(sizes)
+        for lp, r in zip(lps, res):
+            with hpr.Solver(lp, max_iter=CAP) as s:
+                solo = s.solve(1e-8)
+            assert (solo["info"]["path"], solo["info"]["path_ctas"]) == (r["info"]["path"], r["info"]["path_ctas"])
+            assert r["status"] == solo["status"] and r["info"]["iters"] == solo["info"]["iters"], lp.name
+            for key in ("x", "y", "z"):
+                assert np.array_equal(r[key], solo[key]), (lp.name, key)
+        print("cluster sizes", sorted(sizes), "statuses", [int(r["status"]) for r in res])
+    finally:
+        for s in solvers:
+            s.close()
+    mixed = [hpr.Solver(lp, max_iter=300) for lp in (lps[0], lpgen.planted_medium(3, 0.05))]
+    try:
+        with hpr.Batch(mixed) as b:
+            status, res = b.solve(1e-8)
+            assert b.stats()["periods"] > 0
+        assert [int(r["info"]["path"]) for r in res] == [0, 0]
+    finally:
+        for s in mixed:
             s.close()
 
 
