@@ -629,7 +629,10 @@ int cluster_dims(hpr_ctx *ctx, int G, hprgrid::ClusterDims *out)
         CK(cudaMemcpy(sptr.data(), M.sptr, sizeof(int) * sptr.size(), cudaMemcpyDeviceToHost));
         std::vector<int64_t> ent(G, 0), rows(G, 0), nsl(G, 0);
         for (int sl = 0; sl < M.nslices; ++sl) {
-            const int cta = (sl % (G * NW)) % G;   // warp g = warp * G + CTA owns slices g (mod G * NW)
+            // warp g owns slices g (mod G * NW); g = warp * G + CTA for A, and
+            // warp * G + (CTA + G/2) mod G for A^T
+            const int r = (sl % (G * NW)) % G;
+            const int cta = which ? r : (r - G / 2 + G) % G;
             ent[cta] += sptr[sl + 1] - sptr[sl];
             rows[cta] += srow[sl + 1] - srow[sl];
             nsl[cta] += 1;

@@ -8,7 +8,8 @@
 // L2 or HBM access at all:
 //   - each CTA keeps a copy of the slices of A and A^T that its warps own (the same
 //     sliced-ELL layouts and the same slice-to-warp assignment as the persistent grid
-//     path: warp g = warp * G + CTA takes slices g, g + G*NW, ...), with their metadata;
+//     path: warp g takes slices g, g + G*NW, ..., g = warp * G + CTA for A and
+//     warp * G + (CTA + G/2) mod G for A^T), with their metadata;
 //   - each CTA keeps the state of its own rows: x, x0, c, l, u for the rows of A^T, y0 and
 //     b (and the inequality flags) for the rows of A;
 //   - every CTA keeps a replica of the two vectors that the SpMVs gather: y (gathered by
@@ -182,7 +183,9 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
 {
     using hprsmall::now_ns;
     const int tid = threadIdx.x, G = P.G;
-    const int gw = (tid >> 5) * G + rank, GW = G * NW;   // CTA-minor warp numbering
+    // the grid path's warp numbering (A^T's slices start half the cluster further on)
+    const int GW = G * NW;
+    const int gwA = (tid >> 5) * G + rank, gwT = (tid >> 5) * G + (rank + G / 2) % G;
     const int n = P.n, m = P.m;
     double *xb = P.xb, *zb = P.zb, *dx = P.dx, *yb = P.yb, *dy = P.dy;
     __shared__ double red[NQG * NW];
@@ -206,14 +209,14 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
     const uint64_t t_start = now_ns();
 
     int sT0, nT, sA0, nA;
-    cl_stage(P.T, gw, GW, valT, colT, metaT, wtab, &sT0, &nT, [&](int j, int lj) {
+    cl_stage(P.T, gwT, GW, valT, colT, metaT, wtab, &sT0, &nT, [&](int j, int lj) {
         ox[lj] = 0.0;                         // Algorithm 2 from the origin (Section 4.1)
         ox0[lj] = 0.0;
         oc[lj] = __ldg(P.c + j);
         ol[lj] = __ldg(P.l + j);
         ou[lj] = __ldg(P.u + j);
     });
-    cl_stage(P.A, gw, GW, valA, colA, metaA, wtab, &sA0, &nA, [&](int i, int li) {
+    cl_stage(P.A, gwA, GW, valA, colA, metaA, wtab, &sA0, &nA, [&](int i, int li) {
         oy0[li] = 0.0;
         ob[li] = __ldg(P.b + i);
         oineq[li] = __ldg(P.ineq + i);

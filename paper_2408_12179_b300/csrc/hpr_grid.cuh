@@ -17,9 +17,9 @@
 //
 // Work split: warp g of the grid takes slices g, g + G*NW, ... of the same sliced-ELL
 // layouts the multi-CTA path uses, for the whole solve, with the warps numbered CTA-minor
-// (g = warp * G + CTA): consecutive slices go to different CTAs, so the longest slices
-// (rows are numbered by decreasing length) spread over all CTAs instead of all landing in
-// the first one.  Every vector that
+// (g = warp * G + CTA for A, g = warp * G + (CTA + G/2) mod G for A^T): consecutive slices
+// go to different CTAs, so the longest slices (rows are numbered by decreasing length)
+// spread over all CTAs instead of all landing in the first one.  Every vector that
 // this launch writes is written and read through L2 (st/ld.global.cg), never through a
 // possibly stale L1 line of another SM; the matrices and the LP data are read-only.
 //
@@ -323,7 +323,10 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
 {
     using hprsmall::now_ns;
     const int tid = threadIdx.x, G = P.G;
-    const int gw = (tid >> 5) * G + blockIdx.x, GW = G * NW;   // CTA-minor warp numbering
+    // CTA-minor warp numbering; A^T's slices start half the grid further on, so that the
+    // longest slices of A and of A^T do not land in the same CTA
+    const int GW = G * NW;
+    const int gwA = (tid >> 5) * G + (int)blockIdx.x, gwT = (tid >> 5) * G + ((int)blockIdx.x + G / 2) % G;
     const hprsmall::SmallMat MA = P.A, MT = P.T;
     const int n = P.n, m = P.m;
     double *x = P.x, *x0 = P.x0, *xh = P.xh, *xb = P.xb, *zb = P.zb, *dx = P.dx;
@@ -361,13 +364,13 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
         for (;;) {
             const double inv = sc[0];
             double q[2] = {0.0, 0.0};
-            grid_rows(MT, yb, gw, GW, [&](int j, double sj) {
+            grid_rows(MT, yb, gwT, GW, [&](int j, double sj) {
                 const double t = sj * inv;
                 __stcg(dx + j, t);
                 q[0] = fma(t, t, q[0]);
             });
             if (!grid_sync(P, nb++, &s_ok)) return;
-            grid_rows(MA, dx, gw, GW, [&](int i, double wi) {
+            grid_rows(MA, dx, gwA, GW, [&](int i, double wi) {
                 __stcg(yb + i, wi);
                 q[1] = fma(wi, wi, q[1]);
             });
@@ -437,7 +440,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
         double q[NQG] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         // phase X: eq. (update-x), reflection, Halpern step (after a restart: x = x0 = x_bar,
         // y = y_bar, Algorithm 2's w^{r+1,0} = w_bar^{r,tau_r})
-        grid_rows(MT, fresh ? yb : y, gw, GW, [&](int j, double sj) {
+        grid_rows(MT, fresh ? yb : y, gwT, GW, [&](int j, double sj) {
             double xj, x0j;
             if (!fresh) {
                 xj = __ldcg(x + j);
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
         // them after its decisions instead)
         if (!store && tid == NT - 1) set_weights(t_all + 1);
         // phase Y: eq. (update-y-2), projection on D, reflection, Halpern step
-        grid_rows(MA, xh, gw, GW, [&](int i, double qi) {
+        grid_rows(MA, xh, gwA, GW, [&](int i, double qi) {
             double yi, y0i;
             if (!fresh) {
                 yi = __ldcg(y + i);
@@ -500,17 +503,17 @@ __global__ void __launch_bounds__(NT) k_solve_grid(GridArgs P)
             continue;
         }
         // the check quantities: residual passes in the original-space weights, <dy, A dx>
-        grid_rows(MT, yb, gw, GW, [&](int j, double sj) {
+        grid_rows(MT, yb, gwT, GW, [&](int j, double sj) {
             const double rj = __ldg(P.wc + j) * (__ldg(P.c + j) - sj - __ldcg(zb + j));
             q[7] = fma(rj, rj, q[7]);
         });
-        grid_rows(MA, xb, gw, GW, [&](int i, double si) {
+        grid_rows(MA, xb, gwA, GW, [&](int i, double si) {
             double ri = __ldg(P.b + i) - si;
             if (P.ineq[i]) ri = hprdev::pos_part(ri);
             ri *= __ldg(P.wr + i);
             q[8] = fma(ri, ri, q[8]);
         });
-        grid_rows(MA, dx, gw, GW, [&](int i, double si) { q[9] = fma(__ldcg(dy + i), si, q[9]); });
+        grid_rows(MA, dx, gwA, GW, [&](int i, double si) { q[9] = fma(__ldcg(dy + i), si, q[9]); });
         cta_publish<NQG>(q, red, P.partials, G, blockIdx.x);
         if (!grid_sync(P, nb++, &s_ok)) return;
         grid_sums_then<NQG>(P.partials, G, [&](const double *sums) {

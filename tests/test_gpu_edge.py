@@ -1,4 +1,4 @@
-"""Degenerate LPs on both CUDA paths (multi-CTA and persistent single-CTA) against the
+"""Degenerate LPs on the CUDA paths (multi-CTA, persistent single-CTA and persistent cluster) against the
 oracle: fixed variables (l = u), a pure feasibility problem (c = 0), all-free columns, and
 an infeasible LP (the solve must stop at the iteration cap with finite output, not fail)."""
 import numpy as np
@@ -45,7 +45,7 @@ def _all_free(seed):
 CASES = {"fixed": _fixed, "feasibility": _feasibility, "all_free": _all_free}
 
 
-@pytest.mark.parametrize("persistent", [0, 2])
+@pytest.mark.parametrize("persistent", [0, 2, 4])
 @pytest.mark.parametrize("name", list(CASES))
 def test_degenerate_lps(name, persistent):
     lp = CASES[name](3)
@@ -60,7 +60,7 @@ def test_degenerate_lps(name, persistent):
     assert K.in_C(res["x"], lp.l, lp.u) and K.in_D(res["y"], lp.m1)
 
 
-@pytest.mark.parametrize("persistent", [0, 2])
+@pytest.mark.parametrize("persistent", [0, 2, 4])
 def test_infeasible_lp_stops_at_the_cap(persistent):
     """x1 + x2 = 1 and x1 + x2 >= 3 with 0 <= x <= 10: no feasible point.  The solve runs to
     max_iter and returns HPR_MAX_ITER with finite iterates and a primal residual that stays

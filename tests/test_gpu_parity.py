@@ -144,6 +144,31 @@ def test_first_100_iterates(name):
     print(name, "worst entrywise error (floor 1e-6 ||.||_inf):", worst)
 
 
+@pytest.mark.parametrize("persistent", [2, 3, 4])
+@pytest.mark.parametrize("name", list(CASES))
+def test_first_100_iterates_persistent_paths(name, persistent):
+    """The persistent paths (single CTA, grid, cluster) take no trace: after 100 iterations
+    with lambda fixed (no restart decision before the cap) their returned w_bar (x_bar,
+    y_bar, z_bar of iteration 100) against the oracle's, normwise 1e-11 and entry by entry."""
+    lp = CASES[name]()
+    N = 100
+    ref = oracle.solve(lp, max_iter=N)
+    lam = ref["info"]["lambda"]
+    with hpr.Solver(lp, max_iter=N, lambda_fixed=lam, persistent=persistent) as s:
+        try:
+            res = s.solve(1e-12)
+        except hpr.HprError as e:                    # the LP does not fit that path's memory
+            assert e.code == hpr.HPR_ERR_ARG and "cannot run" in str(e), str(e)
+            pytest.skip(str(e))
+    assert res["status"] == hpr.HPR_MAX_ITER and res["info"]["path"] == persistent
+    for key in ("x", "y", "z"):
+        if np.linalg.norm(ref[key]) == 0.0:
+            assert np.linalg.norm(res[key]) <= 1e-300, key
+            continue
+        assert rel(res[key], ref[key]) <= 1e-11, (key, rel(res[key], ref[key]))
+        assert elem(res[key], ref[key], 1e-6) <= 1e-8, (key, elem(res[key], ref[key], 1e-6))
+
+
 @pytest.mark.parametrize("seed", range(5))
 def test_full_solve_tiny(seed):
     lp = lpgen.planted_tiny(seed)
