@@ -488,7 +488,8 @@ def run_ours(args):
         p_ev1.record(stream)
         torch.cuda.synchronize()
         plain = {"time_to_kkt_1e-8_s": p_ev0.elapsed_time(p_ev1) / 1e3, "iters": pinfo["iters"],
-                 "status": hpr.hpr_status_str(int(pinfo["status"])), "final_kkt": pinfo["kkt"]}
+                 "status": hpr.hpr_status_str(int(pinfo["status"])), "final_kkt": pinfo["kkt"],
+                 "primal_obj": pinfo["primal_obj"], "dual_obj": pinfo["dual_obj"]}
         solver.set_options(precision=args.precision)
     solver.close()
 
@@ -541,6 +542,7 @@ def run_ours(args):
         "time_to_kkt_1e-8_s": statistics.mean(t8), "time_to_kkt_1e-4_s": statistics.mean(t4),
         "iters_to_kkt_1e-8": infos[-1]["iters"], "iters_to_kkt_1e-4": infos[-1]["iters_to_1e4"],
         "status": hpr.hpr_status_str(int(infos[-1]["status"])), "final_kkt": infos[-1]["kkt"],
+        "primal_obj": infos[-1]["primal_obj"], "dual_obj": infos[-1]["dual_obj"],
         "restarts": infos[-1]["restarts"], "power_iters": infos[-1]["power_iters"],
         "power_rel_change": infos[-1]["power_rel_change"],
         "iters_fp32": infos[-1]["iters_fp32"],

@@ -32,8 +32,10 @@
  *                          path are replaced by NaN on the host after read-back: the solve
  *                          returns HPR_ERR_NUMERIC;
  *   HPR_FAULT_BARRIER=n    persistent grid path (persistent = 3): its last CTA skips its
- *                          arrival at grid barrier n-1 and every wait's budget drops to
- *                          200 us: the solve returns HPR_ERR_DEVICE_TIMEOUT.
+ *                          arrival at grid barrier n-1; persistent cluster path: its last
+ *                          CTA does not send its rows of x_hat in iteration n-1.  Every
+ *                          wait's budget drops to 200 us: the solve returns
+ *                          HPR_ERR_DEVICE_TIMEOUT.
  * and, for measurements, HPR_GRID_CTAS=G: the CTA count of the persistent grid path (at
  * most one per SM) and of the cluster path (at most 16; the largest resident cluster up to
  * G is taken); unset or 0: chosen from the FP64 work of an iteration.
@@ -141,10 +143,13 @@ typedef struct {
                                  time limit or policy only):
                                    single-CTA: one CTA of 1024 threads, iterates in shared memory
                                    (LPs with 48 n + 32 m bytes <= 200 KB);
-                                   cluster: one thread-block cluster of up to 16 CTAs, hardware
-                                   cluster barriers between the two phases of an iteration, y and
-                                   x_hat replicated in every CTA's shared memory (LPs with
-                                   8 (m + n) bytes within one CTA's shared memory, ~227 KB);
+                                   cluster: one thread-block cluster of up to 16 CTAs, y and
+                                   x_hat replicated in every CTA's shared memory and filled by
+                                   stores that count on a transaction barrier per replica, each
+                                   wait bounded (HPR_ERR_DEVICE_TIMEOUT), the CTAs' slices of A
+                                   and A^T and their rows in their own shared memory (LPs with
+                                   8 (m + n) bytes plus a CTA's share of the matrices within one
+                                   CTA's shared memory, ~227 KB);
                                    grid: one cooperative launch of up to one CTA per SM, software
                                    grid barriers with a bounded wait (HPR_ERR_DEVICE_TIMEOUT when
                                    a wait runs out), gathers through L2.

@@ -233,6 +233,11 @@ int batch_cluster_launch(hpr_batch *b, double tol, BatchClusters &bc)
             int st = small_prepare(c, tol, A, &smem_small);   // solve state, record and result buffers
             if (st) return st;
             if (!c->grid_partials && (st = dalloc(c, &c->grid_partials, grid_partials_len(c)))) return st;
+            if (!c->grid_bar && (st = dalloc(c, &c->grid_bar, 1))) return st;
+            if (cudaMemsetAsync(c->grid_bar, 0, sizeof(GridBar), b->stream) != cudaSuccess) {
+                g_static_err = "hpr_batch_solve: error word could not be cleared";
+                return HPR_ERR_CUDA;
+            }
             ClusterJob J{};
             J.P = grid_args(c, A, G);
             J.CD = dims[e.second];
@@ -298,6 +303,12 @@ int batch_cluster_collect(hpr_batch *b, BatchClusters &bc, int *worst)
         hpr_ctx *c = b->ctxs[i];
         c->grid_ctas_used = bc.size[i];
         c->path_used = 4;
+        hprgrid::GridBar hb{};
+        if (cudaMemcpy(&hb, c->grid_bar, sizeof hb, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            g_static_err = "hpr_batch_solve: error word could not be read";
+            return HPR_ERR_CUDA;
+        }
+        if (hb.err) return cluster_timeout(c, hb);
         const int st = small_collect(c);
         if (st < 0) return st;
         if (st != HPR_OK && *worst == HPR_OK) *worst = st;

@@ -410,13 +410,13 @@ constexpr size_t SMALL_SMEM_MAX = 200 * 1024;
 // ~17 cycles each.  Measured on the tiny planted LP, QAPs (N = 5, 6) and medium planted LPs
 // at 1/1000 .. 1/200 scale, an iteration of the single CTA costs ~1.5 us + 8.4 ns per such
 // instruction, and the multi-CTA graph path ~5 us (launch-bound) or more; the default takes
-// the single CTA up to 600 instructions (~6.5 us) against the multi-CTA path, and up to 250
-// (~4 us) when the persistent cluster path can run the LP: one CTA of a cluster issues only
-// its share of the FP64 work, and the cluster's iterations cost ~3.7 us and up (measured on
-// the medium planted LP at 1/1000 scale, 587 instructions: 7.4 us in one CTA, 4.2 us in a
-// cluster of 4).
+// the single CTA up to 600 instructions (~6.5 us) against the multi-CTA path, and up to 200
+// (~3.1 us) when the persistent cluster path can run the LP: one CTA of a cluster issues only
+// its share of the FP64 work, and the cluster's iterations cost ~3.3 us and up (measured: the
+// tiny planted LP, 172 instructions, 2.85 us in one CTA and 3.33 us in a cluster; the medium
+// planted LP at 1/1000 scale, 587 instructions, 7.13 us in one CTA and 3.84 us in a cluster of 4).
 constexpr double SMALL_FP64_MAX = 600.0;
-constexpr double SMALL_FP64_VS_CLUSTER = 250.0;
+constexpr double SMALL_FP64_VS_CLUSTER = 200.0;
 
 double small_fp64_per_iter(const hpr_ctx *ctx)
 {
@@ -564,11 +564,11 @@ constexpr int CLUSTER_MAX_CTAS = 16;                     // the largest (non-por
 // instructions per CTA, 2 to 16), and the largest work it takes by default, counted as the
 // FP64 warp instructions of an iteration plus a quarter of the rows (each row's result is
 // stored into every CTA's replica).  Measured per iteration against the multi-CTA graph path
-// (3,000 iterations): medium planted LPs at 1/1000 .. 1/100 scale 4.2 / 4.8 / 5.0 / 7.3 us
-// against 7.6 / 7.8 / 8.4 / 8.4 (work 760 .. 7,150), QAP N = 8 4.9 against 6.7 (4,450),
-// N = 9 6.0 against 6.0 (7,000); slower above: the medium LP at 1/80 scale 8.5 against 9.0
-// (8,900: about even), the multicommodity-flow LP with 300 nodes 7.4 against 6.4 (8,400),
-// QAP N = 10 8.7 against 7.0 (10,600).
+// (3,000 iterations): medium planted LPs at 1/1000 .. 1/100 scale 3.8 / 4.2 / 4.4 / 6.7 us
+// against 7.1 / 7.6 / 8.2 / 8.4 (work 760 .. 7,150), QAP N = 8 4.6 against 7.5 (4,450),
+// N = 9 5.9 against 6.4 (7,000); above it the medium LP at 1/80 scale 8.1 against 8.8
+// (8,900), the multicommodity-flow LP with 300 nodes 7.5 against 6.6 (8,400), QAP N = 10
+// 8.3 against 7.4 (10,600).
 constexpr double CLUSTER_FP64_PER_CTA = 150.0;
 constexpr double CLUSTER_WORK_MAX = 7500.0;
 
@@ -689,6 +689,14 @@ const char *cluster_unfit(hpr_ctx *ctx, bool forced)
     return nullptr;
 }
 
+// a wait of the cluster path for a replica's fill ran out of its time budget
+int cluster_timeout(hpr_ctx *ctx, const hprgrid::GridBar &hb)
+{
+    return fail_arg(ctx, HPR_ERR_DEVICE_TIMEOUT,
+                    "persistent cluster solve: a wait for a replica's fill at iteration " + std::to_string(hb.where) +
+                        " ran out of its time budget; every CTA left the loop");
+}
+
 int solve_cluster(hpr_ctx *ctx, double tol)
 {
     using namespace hprgrid;
@@ -724,11 +732,16 @@ int solve_cluster(hpr_ctx *ctx, double tol)
     if (G < 2 || cfg.dynamicSmemBytes == 0 || cluster_smem_bytes((int)ctx->m, (int)ctx->n, d) > limit)
         return fail_arg(ctx, HPR_ERR_ARG, "persistent cluster path: no cluster of two or more CTAs holds the LP");
     if (!ctx->grid_partials) DALLOC(ctx->grid_partials, grid_partials_len(ctx));
+    if (!ctx->grid_bar) DALLOC(ctx->grid_bar, 1);
     GridArgs P = grid_args(ctx, A, G);
+    CK(cudaMemsetAsync(ctx->grid_bar, 0, sizeof(GridBar), ctx->stream));
     CK(cudaLaunchKernelEx(&cfg, k_solve_cluster, P, d));
+    GridBar hb{};
+    CK(cudaMemcpyAsync(&hb, ctx->grid_bar, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->grid_ctas_used = G;
     ctx->path_used = 4;
+    if (hb.err) return cluster_timeout(ctx, hb);
     return small_collect(ctx);
 }
 

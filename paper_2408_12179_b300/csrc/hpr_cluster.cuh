@@ -14,18 +14,21 @@
 //     b (and the inequality flags) for the rows of A;
 //   - every CTA keeps a replica of the two vectors that the SpMVs gather: y (gathered by
 //     the x step, eq. update-x) and x_hat (gathered by the y step, eq. update-y-2).  The
-//     lane that computes an entry stores it into all G replicas (distributed shared memory
-//     stores), and the cluster's hardware barrier between the two steps orders those
-//     stores before the gathers of the next step.  No replica is written in the step that
-//     gathers it.  The power method uses the same replicas for w and s.
+//     lane that computes an entry stores it into all G replicas with st.async, each store
+//     counting its bytes on the receiving CTA's transaction barrier (mbarrier) for that
+//     replica; a CTA gathers from a replica once the barrier's phase for the iteration has
+//     completed.  No cluster barrier is needed in a normal iteration (the ordering argument
+//     is at the main loop).  The power method uses the same replicas for w and s, with
+//     plain remote stores and cluster barriers.
 // A check iteration also writes x_bar, z_bar, dx, y_bar, dy to global memory; the check's
-// residual passes gather those through L2, and a restart reloads the replica of y and the
-// own rows' anchors from them.
+// residual passes gather those through L2 after a cluster barrier, and a restart reloads
+// the replica of y and the own rows' anchors from them.
 //
 // The row sums (two FMA chains, even and odd steps, then a fixed butterfly), the updates
 // and the per-CTA partial sums are those of the persistent grid path with the same number
-// of CTAs, so the two paths give bitwise the same results.  The barriers are hardware
-// barriers of a co-scheduled cluster: there is no software wait to bound.
+// of CTAs, so the two paths give bitwise the same results.  Every wait for a replica's fill
+// is bounded: past its budget the CTA raises the error word and leaves the loop, and the
+// host reports HPR_ERR_DEVICE_TIMEOUT.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -82,6 +85,53 @@ __device__ __forceinline__ uint32_t peer_addr(const void *local, uint32_t rank)
 __device__ __forceinline__ void st_peer(uint32_t addr, double v)
 {
     asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+// ---- transaction-count barriers (mbarrier) for the replicas' fills
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mb, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
+}
+
+// makes the initialisation of this CTA's mbarriers visible to the cluster
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// this CTA's one arrival for the current phase, expecting `bytes` of stores into it
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mb, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes)
+                 : "memory");
+}
+
+// whether the phase of parity `parity` has completed (the stores counted by it are visible)
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mb, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(mb)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// an 8-byte store into a CTA of the cluster that counts 8 bytes on that CTA's mbarrier
+// (addresses from peer_addr)
+__device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t mbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(addr), "d"(v),
+                 "r"(mbar)
+                 : "memory");
 }
 
 __device__ __forceinline__ int warp_sum_int(int v)
@@ -195,6 +245,9 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
     __shared__ int bc_restart, bc_stop;
     __shared__ double sc_in[2];
     __shared__ uint32_t s_peer_y[CL_MAX], s_peer_xh[CL_MAX];
+    __shared__ uint32_t s_peer_mby[CL_MAX], s_peer_mbxh[CL_MAX];
+    __shared__ __align__(8) uint64_t mb_y, mb_xh;   // fills of the replicas (one phase each per iteration)
+    __shared__ int s_err;
     __shared__ int wtab[3 * NW];
     extern __shared__ __align__(16) unsigned char cl_smem[];
     double *const s_y = reinterpret_cast<double *>(cl_smem);    // replica of y (m)
@@ -221,11 +274,20 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
         ob[li] = __ldg(P.b + i);
         oineq[li] = __ldg(P.ineq + i);
     });
+    if (tid == 0) {
+        mbar_init(&mb_y, 1);
+        mbar_init(&mb_xh, 1);
+        fence_mbar_init();
+        s_err = 0;
+    }
     if (tid < G) {
         s_peer_y[tid] = peer_addr(s_y, tid);
         s_peer_xh[tid] = peer_addr(s_xh, tid);
+        s_peer_mby[tid] = peer_addr(&mb_y, tid);
+        s_peer_mbxh[tid] = peer_addr(&mb_xh, tid);
     }
-    cluster_barrier();                        // every CTA runs before any store to a peer
+    cluster_barrier();                        // every CTA runs, and its mbarriers are set, before
+                                              // any store to a peer
 
     // entry idx of a replica, in every CTA of the cluster (this one included)
     auto bcast = [&](const uint32_t *peer, int idx, double v) {
@@ -313,12 +375,45 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
     for (int i = tid; i < m; i += NT) s_y[i] = 0.0;
     cluster_barrier();
 
+    // Normal iterations run without cluster barriers: each replica's fill for an iteration
+    // is one phase of its mbarrier (this CTA's one arrival expecting 8 bytes per entry, and
+    // every entry stored into it by st.async, which counts its bytes there); a CTA waits for
+    // the phase before it gathers.  No replica is refilled while a CTA still gathers from it:
+    // a CTA sends x_hat(k+1) only once its replica of y(k) is complete, that is after every
+    // warp of every CTA has sent its rows of y(k), each after its own gathers of x_hat(k); and
+    // the same for y.  Each wait is bounded (P.budget_ns): past it the CTA raises the error
+    // word and leaves the loop, and every CTA still meets the others at the final barrier.
+    unsigned par_y = 0, par_xh = 0;           // parity of each mbarrier's current phase
+    bool y_pending = false;                   // a fill of the replica of y is under way
+    auto fill_done = [&](uint64_t *mb, unsigned bytes, unsigned &par, int64_t where) -> bool {
+        if (tid == 0) mbar_arrive_expect_tx(mb, bytes);
+        const uint64_t t0 = now_ns();
+        unsigned polls = 0;
+        while (!mbar_try_wait(mb, par)) {
+            if ((++polls & 63u) == 0 && now_ns() - t0 > P.budget_ns) {
+                if (atomicExch(&P.bar->err, 1) == 0) P.bar->where = (int)where;
+                s_err = 1;
+                break;
+            }
+        }
+        par ^= 1u;
+        __syncthreads();
+        return s_err == 0;
+    };
+    auto bcast_async = [&](const uint32_t *peer, const uint32_t *peer_mb, int idx, double v) {
+        for (int d = 0; d < G; ++d) st_async(peer[d] + 8u * (uint32_t)idx, v, peer_mb[d]);
+    };
+
     int64_t k = 0;
     OuterState D;
     int64_t t_all = 0;
     int64_t to_check = P.check_every;
 #pragma unroll 1
     for (k = 0; k < P.max_iter; ++k) {
+        if (y_pending) {                      // y(k) complete in this CTA's replica
+            if (!fill_done(&mb_y, 8u * (unsigned)m, par_y, k)) break;
+            y_pending = false;
+        }
         const double sigma = bc_sigma, ha = bc_ha, hb = bc_hb, inv_ls = bc_ils;
         const bool periodic = (--to_check == 0);
         if (periodic) to_check = P.check_every;
@@ -333,7 +428,8 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
             const double v = fma(sigma, sj - cj, xj);
             const double xbj = hprdev::clamp_lu(v, lj_, uj);
             const double xhj = fma(2.0, xbj, -xj);
-            bcast(s_peer_xh, j, xhj);
+            if (!(rank == P.skip_cta && k == (int64_t)P.skip_at))      // fault injection: a lost fill
+                bcast_async(s_peer_xh, s_peer_mbxh, j, xhj);
             ox[lj] = fma(hb, P.reflect ? xhj : xbj, ha * x0j);
             if (store) {
                 const double zbj = (xbj - v) / sigma, d = xj - xbj, e = xbj - x0j;
@@ -347,9 +443,9 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
                 else if (zbj < 0.0) q[3] = fma(zbj, uj, q[3]);
             }
         });
-        cluster_barrier();
+        if (!fill_done(&mb_xh, 8u * (unsigned)n, par_xh, k)) break;   // x_hat(k) complete
         // the next iteration's weights, by the last thread while the others update y: every
-        // thread read this iteration's values before the barrier above
+        // thread of this CTA read this iteration's values before the wait above
         if (!store && tid == NT - 1) set_weights(t_all + 1);
         // y step: eq. (update-y-2), projection on D, reflection, Halpern step
         rowsA(from_xh, [&](int i, int li, double qi) {
@@ -358,7 +454,7 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
             double ybi = fma(bi - qi, inv_ls, yi);
             if (oineq[li]) ybi = hprdev::pos_part(ybi);
             const double yhi = fma(2.0, ybi, -yi);
-            bcast(s_peer_y, i, fma(hb, P.reflect ? yhi : ybi, ha * y0i));
+            bcast_async(s_peer_y, s_peer_mby, i, fma(hb, P.reflect ? yhi : ybi, ha * y0i));
             if (store) {
                 const double d = yi - ybi, e = ybi - y0i;
                 __stcg(yb + i, ybi);
@@ -368,11 +464,12 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
                 q[6] = fma(bi, ybi, q[6]);
             }
         });
-        cluster_barrier();
+        y_pending = true;
         if (!store) {
             ++t_all;
             continue;
         }
+        cluster_barrier();                    // the check's global stores, seen by every CTA
         // the check quantities: residual passes in the original-space weights, <dy, A dx>
         rowsT([&](int c) { return __ldcg(yb + c); }, [&](int j, int lj, double sj) {
             const double rj = __ldg(P.wc + j) * (oc[lj] - sj - __ldcg(zb + j));
@@ -404,9 +501,12 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
         }
         if (bc_restart) {
             // w^{r+1,0} = w_bar (Algorithm 2): the replica of y and the own rows' x, x0, y0
-            // take y_bar and x_bar (written before the last two barriers; no peer stores
-            // into the replica before the next y step)
+            // take y_bar and x_bar (written before the last two barriers).  The replica's
+            // fill with y(k+1) completes first; no peer stores into it again before this CTA
+            // has sent its rows of x_hat(k+1).
             t_all = 0;
+            if (!fill_done(&mb_y, 8u * (unsigned)m, par_y, k)) break;
+            y_pending = false;
             for (int i = tid; i < m; i += NT) s_y[i] = __ldcg(yb + i);
             cl_own_rows(metaT, sT0, nT, [&](int j, int lj) {
                 const double v = __ldcg(xb + j);
@@ -419,7 +519,10 @@ __device__ __forceinline__ void cluster_solve(const GridArgs &P, const ClusterDi
             ++t_all;
         }
     }
-    cluster_barrier();                        // no CTA leaves while a peer may still store to it
+    // no CTA leaves while a peer may still store to it: the last fill of y lands, then the
+    // cluster meets (after an error the fill may never complete: its wait is bounded too)
+    if (y_pending && s_err == 0) (void)fill_done(&mb_y, 8u * (unsigned)m, par_y, k);
+    cluster_barrier();
     if (rank == 0 && tid == 0) write_out(P, D, k, lambda, piters, bc_sigma, prel, t_start, t_power);
 }
 

@@ -11,7 +11,8 @@ and its rows' state in its own shared memory) against the oracle.
 * 100 iterations with lambda fixed: the returned w_bar against the oracle's, normwise 1e-11
   and entry by entry, bitwise the same for every cluster size, on the grid path and on the
   single-CTA path;
-* LPs whose data do not fit in the cluster's shared memory, and the FP32 form, are refused.
+* LPs whose data do not fit in the cluster's shared memory, and the FP32 form, are refused;
+* a lost fill of a replica (host-injected) ends in HPR_ERR_DEVICE_TIMEOUT, not a hang.
 """
 import os
 
@@ -113,6 +114,27 @@ def test_cluster_first_100_iterations(name, sizes):
     if name == "tiny0":                              # the single-CTA path does the same row arithmetic
         res = hpr.solve(lp, tol=1e-12, max_iter=N, lambda_fixed=lam, persistent=2)
         assert np.array_equal(_wbar(res), outs[0])
+
+
+def test_cluster_fill_timeout_is_reported():
+    """A CTA that does not send its rows of x_hat in one iteration (HPR_FAULT_BARRIER,
+    host-injected) leaves every CTA's wait for that fill to run out of its budget (200 us
+    under injection): the solve returns HPR_ERR_DEVICE_TIMEOUT naming the iteration, and the
+    context and the GPU stay usable."""
+    lp = lpgen.planted_medium(0, 0.005)
+    os.environ["HPR_FAULT_BARRIER"] = "5"
+    try:
+        s = hpr.Solver(lp, persistent=4)
+    finally:
+        os.environ.pop("HPR_FAULT_BARRIER", None)
+    with s:
+        with pytest.raises(hpr.HprError) as e:
+            s.solve(1e-8)
+        assert e.value.code == hpr.HPR_ERR_DEVICE_TIMEOUT
+        assert "iteration 4" in str(e.value)
+    ref = oracle.solve(lp, tol=1e-8, max_iter=2_000_000)
+    res = hpr.solve(lp, tol=1e-8, persistent=4)
+    assert res["status"] == hpr.HPR_OK and res["info"]["iters"] == ref["info"]["iters"]
 
 
 def test_cluster_refused_when_it_cannot_run():
