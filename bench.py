@@ -186,6 +186,8 @@ def workload(args):
         return lpgen.qap_lp(args.seed, args.qap_n)
     if args.workload == "tiny":
         return lpgen.planted_tiny(args.seed)
+    if args.workload == "mid":                     # the reference arm: its 1/200-scale LP
+        return lpgen.planted_medium(args.seed, 0.005)
     return lpgen.planted_medium(args.seed, args.scale)
 
 
@@ -721,6 +723,79 @@ def run_tiny(args):
     print(json.dumps(line), flush=True)
 
 
+MID_SCALES = (0.001, 0.002, 0.005, 0.01)
+MID_QAPS = (6, 8)
+
+
+def mid_lps(args):
+    """The mid-size workload: medium planted LPs at 1/1000 .. 1/100 scale and two QAP LPs."""
+    from paper_2408_12179_b300 import lpgen
+
+    return ([(f"medium 1/{round(1 / sc)}", lpgen.planted_medium(args.seed, sc)) for sc in MID_SCALES]
+            + [(f"QAP N={q}", lpgen.qap_lp(args.seed + 2, q)) for q in MID_QAPS])
+
+
+def run_mid(args):
+    """Mid-size LPs (too much FP64 work for one SM, too little to fill the GPU): per LP the
+    microseconds per iteration (lambda fixed, 3,000 iterations after a warm-up solve) on the
+    multi-CTA graph path, the persistent single-CTA path and the persistent cluster path (when
+    the LP fits them), and the time to KKT <= tol (power method included) on the graph path
+    and on the default path (which takes the cluster path for these LPs).  value = iterations
+    / s of the default path over all LPs' solves to tol."""
+    import torch
+
+    from paper_2408_12179_b300 import hpr
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    hpr.load()
+    stream = torch.cuda.Stream()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    rows = []
+    launches = 0
+    for name, lp in mid_lps(args):
+        row = {"lp": name, "n": lp.n, "m": lp.m, "nnz": lp.nnz}
+        for label, p in (("graph", 0), ("single_cta", 2), ("cluster", 4)):
+            try:
+                with hpr.Solver(lp, lambda_fixed=1.0, max_iter=3000, persistent=p, cuda_stream=stream.cuda_stream) as s:
+                    s.solve(1e-12)
+                    I = s.solve(1e-12)["info"]
+                row[f"us_per_iter_{label}"] = 1e6 * I["solve_time_s"] / I["iters"]
+            except hpr.HprError:
+                row[f"us_per_iter_{label}"] = None          # the LP does not fit that path
+        for label, p in (("graph", 0), ("default", 1)):
+            with hpr.Solver(lp, max_iter=args.max_iter, persistent=p, cuda_stream=stream.cuda_stream) as s:
+                for _ in range(args.warmup):
+                    s.solve(args.tol)
+                I = s.solve(args.tol)["info"]
+            row[f"time_to_kkt_{label}_s"] = I["solve_time_s"]
+            row[f"iters_{label}"] = int(I["iters"])
+            row[f"status_{label}"] = hpr.hpr_status_str(int(I["status"]))
+            if label == "default":
+                row["default_path"] = {0: "graph", 2: "single_cta", 3: "grid", 4: "cluster"}[int(I["path"])]
+                row["default_ctas"] = int(I["path_ctas"])
+                launches += int(I["launches"])
+        rows.append(row)
+    clocks = sampler.stop()
+    its = sum(r["iters_default"] for r in rows)
+    secs = sum(r["time_to_kkt_default_s"] for r in rows)
+    line = {
+        "metric": "time to KKT <= tol on mid-size LPs: persistent cluster path (default) vs multi-CTA graph path",
+        "value": its / secs, "unit": "iter/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "medium planted LPs at scales " + ", ".join(str(x) for x in MID_SCALES)
+                               + " and QAP LPs N = " + ", ".join(str(q) for q in MID_QAPS) + f" (seed {args.seed})",
+                   "tol": args.tol, "l2": "working sets far below L2 (latency-bound; no flush)"},
+        "time_to_kkt_graph_s_total": sum(r["time_to_kkt_graph_s"] for r in rows),
+        "time_to_kkt_default_s_total": secs,
+        "lps": rows, "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -738,11 +813,12 @@ def parse_args(argv=None):
                     help="0: FP64; 1: FP32 form, then FP64 below KKT 1e-5")
     ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true",
                     help="also time one plain FP64 solve and report it beside the chosen form")
-    ap.add_argument("--workload", choices=["medium", "mcf", "batch", "qap", "tiny", "forms"], default="medium",
+    ap.add_argument("--workload", choices=["medium", "mcf", "batch", "qap", "tiny", "forms", "mid"], default="medium",
                     help="medium sparse planted LP (default), the min-cost multicommodity flow LP "
                          "(1M nodes at scale 1), a batch of uneven planted LPs solved in one "
-                         "batched run (m log-uniform in [500, 50000 * scale]), or the FP32 form "
-                         "against FP64 on --count medium planted LPs at --scale")
+                         "batched run (m log-uniform in [500, 50000 * scale]), the FP32 form "
+                         "against FP64 on --count medium planted LPs at --scale, or mid-size LPs "
+                         "on the persistent cluster path against the multi-CTA path")
     ap.add_argument("--count", type=int, default=None,
                     help="LPs in the batch workload (default 512) or the tiny workload (default 100)")
     ap.add_argument("--qap-n", dest="qap_n", type=int, default=30,
@@ -772,6 +848,8 @@ def main():
     args = parse_args()
     if args.workload == "tiny" and args.impl == "ours":
         run_tiny(args)
+    elif args.workload == "mid" and args.impl == "ours":
+        run_mid(args)
     elif args.workload == "forms":
         run_forms(args)
     elif args.impl == "reference" and args.workload == "batch":

@@ -14,10 +14,11 @@ of the solve) minus log10 KKT at the decision: lower is better.
 
 ``python -m paper_2408_12179_b300.policy eval weights.npy n_eval n_large margin...`` only
 evaluates given weights, once per margin (``policy_margin``).
-``python -m paper_2408_12179_b300.policy [n_train n_eval weights.npy n_large]`` trains on
-seeded small instances of the medium planted and multicommodity-flow families and
+``python -m paper_2408_12179_b300.policy [n_train n_eval weights.npy n_large [large_scale]]``
+trains on seeded small instances of the medium planted and multicommodity-flow families and
 evaluates on held-out ones of the same sizes and on `n_large` held-out medium planted LPs
-at scale 0.05 (25k columns) (one GPU), printing one JSON line.
+at scale `large_scale` (default 0.05: 25k columns) (one GPU), printing one JSON line with a
+95% bootstrap interval of the geometric-mean iteration ratio.
 """
 from __future__ import annotations
 
@@ -112,10 +113,16 @@ def training_family(count, seed0=0):
 
 def summary(rows):
     ok = [r for r in rows if r["rule_status"] == 0 and r["policy_status"] == 0]
-    gm = math.exp(sum(math.log(r["policy_iters"] / r["rule_iters"]) for r in ok) / max(len(ok), 1))
+    logs = np.array([math.log(r["policy_iters"] / r["rule_iters"]) for r in ok])
+    gm = math.exp(float(logs.mean())) if len(logs) else float("nan")
+    ci = [float("nan"), float("nan")]
+    if len(logs) > 1:                         # 95% bootstrap interval of the geometric mean
+        rng = np.random.default_rng(0x5EED)
+        means = rng.choice(logs, size=(2000, len(logs)), replace=True).mean(axis=1)
+        ci = [math.exp(float(np.quantile(means, 0.025))), math.exp(float(np.quantile(means, 0.975)))]
     dec = sum(r["decisions"] for r in rows)
     fb = sum(r["fallbacks"] for r in rows)
-    return dict(n=len(rows), converged_both=len(ok), iters_ratio_geomean=gm,
+    return dict(n=len(rows), converged_both=len(ok), iters_ratio_geomean=gm, iters_ratio_ci95=ci,
                 time_rule_s=sum(r["rule_s"] for r in rows), time_policy_s=sum(r["policy_s"] for r in rows),
                 worse=sum(r["policy_iters"] > r["rule_iters"] for r in ok), decisions=dec, fallbacks=fb,
                 fallback_rate=fb / max(dec + fb, 1))
@@ -139,6 +146,7 @@ def main(argv):
     n_train = int(argv[1]) if len(argv) > 1 else 40
     n_eval = int(argv[2]) if len(argv) > 2 else 10
     n_large = int(argv[4]) if len(argv) > 4 else 0
+    large_scale = float(argv[5]) if len(argv) > 5 else 0.05
     hpr.load()
     t0 = time.time()
     X, A, Y = collect(training_family(n_train, 0), seeds=(11, 12))
@@ -147,9 +155,11 @@ def main(argv):
     t2 = time.time()
     held = training_family(n_eval, 10_000)
     rows = evaluate(held, w)
-    large = evaluate([lpgen.planted_medium(20_000 + i, 0.05) for i in range(n_large)], w) if n_large else []
+    large = (evaluate([lpgen.planted_medium(20_000 + i, large_scale) for i in range(n_large)], w)
+             if n_large else [])
     t3 = time.time()
-    print(json.dumps(dict(samples=int(len(Y)), collect_s=t1 - t0, train_s=t2 - t1, eval_s=t3 - t2,
+    print(json.dumps(dict(samples=int(len(Y)), n_train=n_train, large_scale=large_scale,
+                          collect_s=t1 - t0, train_s=t2 - t1, eval_s=t3 - t2,
                           loss_first=float(hist[0]), loss_last=float(hist[-1]),
                           small=summary(rows), large=summary(large) if large else None,
                           rows=rows, large_rows=large)))

@@ -1,7 +1,7 @@
 """The persistent cluster path (one launch of one thread-block cluster of up to 16 CTAs runs
-the whole solve; hardware cluster barriers between the two phases of Algorithm 2; y and
-x_hat gathered from replicas in every CTA's shared memory, each CTA's slices of A and A^T
-and its rows' state in its own shared memory) against the oracle.
+the whole solve; y and x_hat gathered from replicas in every CTA's shared memory, filled by
+st.async stores counted on a transaction barrier per replica; each CTA's slices of A and
+A^T and its rows' state in its own shared memory) against the oracle.
 
 * full solves at tol 1e-8: lambda to 1e-10, objective within 1e-7 of the oracle's, an
   independently evaluated KKT residual <= tol, and the decision sequence (Section 3.1,
