@@ -181,7 +181,7 @@ int batch_cluster_launch(hpr_batch *b, double tol, BatchClusters &bc)
             return HPR_OK;
         }
         bc.size[i] = G;
-        const double cost = small_fp64_per_iter(cs[i]) + 0.25 * (double)(cs[i]->m + cs[i]->n);
+        const double cost = small_fp64_per_iter(cs[i]) + CLUSTER_ROW_WEIGHT * (double)(cs[i]->m + cs[i]->n);
         groups[G].push_back({cost, i});
     }
     if (cudaFuncSetAttribute(k_solve_cluster_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||

@@ -562,15 +562,17 @@ constexpr uint64_t GRID_FAULT_BUDGET_NS = 200000ull;     // 200 us when a skip i
 constexpr int CLUSTER_MAX_CTAS = 16;                     // the largest (non-portable) cluster
 // cluster path: CTAs from the FP64 work of an iteration (about CLUSTER_FP64_PER_CTA warp
 // instructions per CTA, 2 to 16), and the largest work it takes by default, counted as the
-// FP64 warp instructions of an iteration plus a quarter of the rows (each row's result is
-// stored into every CTA's replica).  Measured per iteration against the multi-CTA graph path
-// (3,000 iterations): medium planted LPs at 1/1000 .. 1/100 scale 3.8 / 4.2 / 4.4 / 6.7 us
-// against 7.1 / 7.6 / 8.2 / 8.4 (work 760 .. 7,150), QAP N = 8 4.6 against 7.5 (4,450),
-// N = 9 5.9 against 6.4 (7,000); above it the medium LP at 1/80 scale 8.1 against 8.8
-// (8,900), the multicommodity-flow LP with 300 nodes 7.5 against 6.6 (8,400), QAP N = 10
-// 8.3 against 7.4 (10,600).
+// FP64 warp instructions of an iteration plus CLUSTER_ROW_WEIGHT per row (each row's value
+// is stored into every CTA's replica).  Fit to the measured iterations of eight LPs at 16
+// CTAs: about 2.4 us + 0.41 ns per FP64 instruction + 0.20 ns per row.  Per iteration against
+// the multi-CTA graph path (3,000 iterations; work in brackets): medium planted LPs at
+// 1/1000 .. 1/100 scale 3.8 / 4.2 / 4.4 / 6.6 us against 7.0 / 7.1 / 8.1 / 8.2 (1,000 ..
+// 10,400), QAP N = 8 4.4 against 7.0 (6,100), N = 9 5.9 against 6.4 (9,700); left to the
+// graph path: the medium LP at 1/80 scale 8.1 against 8.8 (13,000), the multicommodity-flow
+// LP with 300 nodes 7.5 against 6.6 (11,600), QAP N = 10 8.3 against 7.4 (14,500).
 constexpr double CLUSTER_FP64_PER_CTA = 150.0;
-constexpr double CLUSTER_WORK_MAX = 7500.0;
+constexpr double CLUSTER_ROW_WEIGHT = 0.48;
+constexpr double CLUSTER_WORK_MAX = 10500.0;
 
 const char *grid_unfit(const hpr_ctx *ctx, bool forced)
 {
@@ -676,7 +678,7 @@ size_t cluster_smem_limit(const hpr_ctx *ctx)
 const char *cluster_unfit(hpr_ctx *ctx, bool forced)
 {
     if (const char *why = grid_unfit(ctx, true)) return why;
-    if (!forced && small_fp64_per_iter(ctx) + 0.25 * (double)(ctx->m + ctx->n) > CLUSTER_WORK_MAX)
+    if (!forced && small_fp64_per_iter(ctx) + CLUSTER_ROW_WEIGHT * (double)(ctx->m + ctx->n) > CLUSTER_WORK_MAX)
         return "enough work per iteration to fill the GPU from launches";
     const size_t limit = cluster_smem_limit(ctx);
     const int G = cluster_ctas(ctx);
