@@ -36,9 +36,9 @@ BATCH_METRIC = "HPR iterations/s summed over the LPs of the batch workload (LPs 
 # FP64; see profiles/), valid only for that workload and the kernel source they were
 # taken on.
 NCU_TRAFFIC = {
-    "source_sha1": "4b0111ad65ef731565dd36ad0b399d07e764bbfb",
-    "k_phase_x": 87543296,
-    "k_phase_y": 72115200,
+    "source_sha1": "773e748f071a947ef233fe86cc11a676d2e263e8",
+    "k_phase_x": 87482368,
+    "k_phase_y": 72112128,
 }
 
 

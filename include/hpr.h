@@ -299,6 +299,16 @@ int hpr_power_noalloc(int64_t m, int64_t n, const int32_t *A_row_ptr, const int3
  * its own device buffers (read_bytes + max(4 x L2 size, 256 MiB) + 8 gather_len bytes).
  * Returns HPR_OK, HPR_ERR_ARG, HPR_ERR_NO_DEVICE, HPR_ERR_NOMEM or HPR_ERR_CUDA; detail in
  * hpr_last_error(NULL). */
+/* ---- Bounds-checking build (no counterpart in the paper; a test build standing in for a
+ * memory checker).  Built with HPR_BOUNDS_CHECK, every gather's index -- the sliced-ELL
+ * SpMVs of all paths, the allocation-free power method, the preprocessing's column scaling
+ * and permutation gathers -- is checked against the length of the vector it reads; an index
+ * out of range is counted and replaced by 0, so the load stays in bounds and no kernel
+ * traps.  hpr_bounds_violations waits for the current device and returns the count since
+ * the library was loaded in *count (-1 in the normal build, which checks nothing).  Returns
+ * HPR_OK, HPR_ERR_ARG (count NULL) or HPR_ERR_CUDA. */
+int hpr_bounds_violations(int64_t *count);
+
 int hpr_memory_probe(int64_t read_bytes, int64_t gather_len, void *cuda_stream, double *read_gbs,
                      double *gather_gps);
 

@@ -65,6 +65,7 @@ struct GraphKey {
 // one matrix in the sliced-ELL layout (device arrays; see k_sell)
 struct SellDev {
     int rows = 0, nslices = 0;
+    int cols = 0;                 // length of the vectors it gathers (columns of the matrix)
     int64_t entries = 0;          // stored entries (nonzeros + padding)
     int steps_max = 0;            // layout parameters (build_sell)
     double unit_cost = 0.0;
@@ -492,7 +493,7 @@ SellArgs sell_of(const SellDev &d, bool fp32, const int *skip = nullptr)
 {
     SellArgs a;
     a.rows = d.rows; a.nslices = d.nslices; a.srow = d.srow; a.sptr = d.sptr; a.slg = d.slg;
-    a.wstart = d.wstart; a.nruns = d.nruns; a.col = d.col; a.skip = skip;
+    a.wstart = d.wstart; a.nruns = d.nruns; a.col = d.col; a.cols = d.cols; a.skip = skip;
     a.val = fp32 ? (const void *)d.val32 : (const void *)d.val;
     a.trigger_from = INT32_MAX;
     return a;
@@ -723,7 +724,7 @@ int run_power_small(hpr_ctx *ctx, bool *done)
     hprsmall::SmallArgs A{};
     auto mat_of = [](const SellDev &D) {
         hprsmall::SmallMat M{};
-        M.nslices = D.nslices; M.entries = D.entries;
+        M.nslices = D.nslices; M.cols = D.cols; M.entries = D.entries;
         M.srow = D.srow; M.sptr = D.sptr; M.col = D.col; M.slg = D.slg; M.val = D.val;
         return M;
     };
@@ -870,6 +871,7 @@ int install_layout(hpr_ctx *ctx, SellDev &D, const SellHost &H, int rows, const 
     cudaStream_t s = ctx->stream;
     free_layout(D);
     D.rows = rows; D.nslices = H.nslices;
+    D.cols = (&D == &ctx->ST) ? (int)ctx->m : (int)ctx->n;
     D.steps_max = H.steps_max; D.unit_cost = H.unit_cost;
     D.nruns = (int)H.wstart.size() - 1;
     D.ucost = H.ucost;
@@ -886,7 +888,7 @@ int install_layout(hpr_ctx *ctx, SellDev &D, const SellHost &H, int rows, const 
     if (D.entries) {
         CK(cudaMemcpyAsync(D.col, H.col.data(), sizeof(int) * H.col.size(), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(D.src, H.src.data(), sizeof(int) * H.src.size(), cudaMemcpyHostToDevice, s));
-        k_gather_src<<<grid_for(D.entries), 256, 0, s>>>(D.entries, csr_val, D.src, D.val); CKL();
+        k_gather_src<<<grid_for(D.entries), 256, 0, s>>>(D.entries, csr_val, (int)ctx->nnz, D.src, D.val); CKL();
         k_narrow<<<grid_for(D.entries), 256, 0, s>>>(D.entries, D.val, D.val32); CKL();
     }
     CK(cudaStreamSynchronize(s));
@@ -1061,6 +1063,7 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     ctx->pstride = std::max({gA, gT, (int)((std::max(m, n) + TB - 1) / TB), 1});
     auto upload_sell = [&](SellDev &D, const SellHost &H, int rows) -> int {
         D.rows = rows; D.nslices = H.nslices;
+        D.cols = (&D == &ctx->ST) ? (int)ctx->m : (int)ctx->n;
         D.steps_max = H.steps_max; D.unit_cost = H.unit_cost;
         D.nruns = (int)H.wstart.size() - 1;
         D.ucost = H.ucost;
@@ -1140,7 +1143,7 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
         k_row_absmax<<<gn, 256, 0, s>>>((int)n, ctx->T_rp, ctx->T_val, dc); CKL();
         k_factor<<<gm, 256, 0, s>>>((int)m, dr, ctx->Dr); CKL();
         k_factor<<<gn, 256, 0, s>>>((int)n, dc, ctx->Dc); CKL();
-        k_scale_rows_cols<<<gm, 256, 0, s>>>((int)m, ctx->A_rp, ctx->A_ci, ctx->A_val, dr, dc); CKL();
+        k_scale_rows_cols<<<gm, 256, 0, s>>>((int)m, (int)n, ctx->A_rp, ctx->A_ci, ctx->A_val, dr, dc); CKL();
     }
     if (ctx->opt.pc_alpha >= 0.0) {
         const double al = ctx->opt.pc_alpha;
@@ -1149,7 +1152,7 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
         k_row_abspow<<<gn, 256, 0, s>>>((int)n, ctx->T_rp, ctx->T_val, al, dc); CKL();
         k_factor<<<gm, 256, 0, s>>>((int)m, dr, ctx->Dr); CKL();
         k_factor<<<gn, 256, 0, s>>>((int)n, dc, ctx->Dc); CKL();
-        k_scale_rows_cols<<<gm, 256, 0, s>>>((int)m, ctx->A_rp, ctx->A_ci, ctx->A_val, dr, dc); CKL();
+        k_scale_rows_cols<<<gm, 256, 0, s>>>((int)m, (int)n, ctx->A_rp, ctx->A_ci, ctx->A_val, dr, dc); CKL();
     }
     k_gather<<<gz, 256, 0, s>>>(nnz, ctx->A_val, ctx->T_perm, ctx->T_val); CKL();
 
@@ -1168,8 +1171,8 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
                                                               ctx->l_s, ctx->u_s, ctx->wr, ctx->wc);
     CKL();
     // the iteration's copies: stored values through the position map, vectors renumbered
-    k_gather_src<<<grid_for(ctx->SA.entries), 256, 0, s>>>(ctx->SA.entries, ctx->A_val, ctx->SA.src, ctx->SA.val); CKL();
-    k_gather_src<<<grid_for(ctx->ST.entries), 256, 0, s>>>(ctx->ST.entries, ctx->T_val, ctx->ST.src, ctx->ST.val); CKL();
+    k_gather_src<<<grid_for(ctx->SA.entries), 256, 0, s>>>(ctx->SA.entries, ctx->A_val, (int)ctx->nnz, ctx->SA.src, ctx->SA.val); CKL();
+    k_gather_src<<<grid_for(ctx->ST.entries), 256, 0, s>>>(ctx->ST.entries, ctx->T_val, (int)ctx->nnz, ctx->ST.src, ctx->ST.val); CKL();
     k_narrow<<<grid_for(ctx->SA.entries), 256, 0, s>>>(ctx->SA.entries, ctx->SA.val, ctx->SA.val32); CKL();
     k_narrow<<<grid_for(ctx->ST.entries), 256, 0, s>>>(ctx->ST.entries, ctx->ST.val, ctx->ST.val32); CKL();
     k_permute<<<gm, 256, 0, s>>>(m, ctx->b_s, ctx->perm_r, ctx->bp); CKL();

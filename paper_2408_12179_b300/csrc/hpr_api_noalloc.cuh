@@ -27,7 +27,7 @@ static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
 
 // Warp-per-row variant of k_spmv_norm: out = M xin, partial ||out||^2 per CTA.  No tile
 // schedule is needed, so the caller's plain CSR arrays are enough.
-__global__ void __launch_bounds__(TB) k_rows_spmv_norm(int rows, const int *__restrict__ rp,
+__global__ void __launch_bounds__(TB) k_rows_spmv_norm(int rows, int cols, const int *__restrict__ rp,
                                                        const int *__restrict__ ci,
                                                        const double *__restrict__ val,
                                                        const double *__restrict__ xin, double *out,
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(TB) k_rows_spmv_norm(int rows, const int *__re
     for (int64_t r = (int64_t)blockIdx.x * (TB / 32) + (threadIdx.x >> 5); r < rows; r += warps) {
         double s = 0.0;
         for (int64_t k = (int64_t)rp[r] + lane; k < (int64_t)rp[r + 1]; k += 32)
-            s = fma(val[k], __ldg(xin + ci[k]), s);
+            s = fma(val[k], __ldg(xin + HPR_COL(ci[k], cols)), s);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
@@ -154,11 +154,11 @@ extern "C" int hpr_power_noalloc(int64_t m, int64_t n, const int32_t *A_row_ptr,
     for (int64_t done_steps = 0; done_steps <= max_iter; done_steps += BATCH) {
         for (int k = 0; k < BATCH; ++k) {
             // s = A^T u, lambda_k = ||s||^2, then w = A s written over u and normalised
-            k_rows_spmv_norm<<<gT, TB, 0, st>>>((int)n, At_row_ptr, At_col_idx, At_val, u, s,
+            k_rows_spmv_norm<<<gT, TB, 0, st>>>((int)n, (int)m, At_row_ptr, At_col_idx, At_val, u, s,
                                                 partials, NA_SLOTS, Q_S2, pc);
             k_reduce<<<1, TB, 0, st>>>(partials, NA_SLOTS, rs, scal, &pc->done);
             k_pow_after_s<<<1, 1, 0, st>>>(pc, scal);
-            k_rows_spmv_norm<<<gA, TB, 0, st>>>((int)m, A_row_ptr, A_col_idx, A_val, s, u,
+            k_rows_spmv_norm<<<gA, TB, 0, st>>>((int)m, (int)n, A_row_ptr, A_col_idx, A_val, s, u,
                                                 partials, NA_SLOTS, Q_W2, pc);
             k_reduce<<<1, TB, 0, st>>>(partials, NA_SLOTS, rw, scal, &pc->done);
             k_pow_after_w<<<1, 1, 0, st>>>(pc, scal);

@@ -66,6 +66,27 @@ __global__ void k_probe_fill(uint4 *p, int64_t n)
 
 }  // namespace
 
+extern "C" int hpr_bounds_violations(int64_t *count)
+{
+    if (!count) {
+        g_static_err = "hpr_bounds_violations: count is NULL";
+        return HPR_ERR_ARG;
+    }
+#ifdef HPR_BOUNDS_CHECK
+    unsigned long long v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpyFromSymbol(&v, hprdev::g_bounds_violations, sizeof v) != cudaSuccess) {
+        (void)cudaGetLastError();
+        g_static_err = "hpr_bounds_violations: the counter could not be read";
+        return HPR_ERR_CUDA;
+    }
+    *count = (int64_t)v;
+#else
+    *count = -1;
+#endif
+    return HPR_OK;
+}
+
 extern "C" int hpr_memory_probe(int64_t read_bytes, int64_t gather_len, void *cuda_stream, double *read_gbs,
                                 double *gather_gps)
 {

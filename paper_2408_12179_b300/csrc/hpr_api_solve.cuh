@@ -468,7 +468,7 @@ int small_prepare(hpr_ctx *ctx, double tol, hprsmall::SmallArgs &A, size_t *smem
     if (!ctx->small_out) DALLOC(ctx->small_out, SO_LEN);
     auto mat_of = [](const SellDev &D) {
         SmallMat M{};
-        M.nslices = D.nslices; M.entries = D.entries;
+        M.nslices = D.nslices; M.cols = D.cols; M.entries = D.entries;
         M.srow = D.srow; M.sptr = D.sptr; M.col = D.col; M.slg = D.slg; M.val = D.val;
         return M;
     };

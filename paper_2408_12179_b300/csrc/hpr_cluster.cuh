@@ -176,7 +176,7 @@ __device__ __forceinline__ void cl_stage(const hprsmall::SmallMat &M, int gw, in
         const int g0 = __ldg(M.sptr + s), ne = __ldg(M.sptr + s + 1) - g0;
         for (int t = lane; t < ne; t += 32) {
             val[pe + t] = __ldg(M.val + g0 + t);
-            col[pe + t] = __ldg(M.col + g0 + t);
+            col[pe + t] = HPR_COL(__ldg(M.col + g0 + t), M.cols);
         }
         const int r0 = __ldg(M.srow + s), r1 = __ldg(M.srow + s + 1);
         if (lane == 0) meta[bs + i] = SlMeta{r0, r1, pe, pr, ne >> 5, (int)__ldg(M.slg + s)};

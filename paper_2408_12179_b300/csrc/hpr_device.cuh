@@ -25,6 +25,26 @@
 
 namespace hprdev {
 
+// ---- bounds-checking build (HPR_BOUNDS_CHECK): every gather's index is checked against
+// the gathered vector's length before the load; an index out of range is counted in a
+// device counter (read with hpr_bounds_violations) and replaced by 0, so that the load
+// stays in bounds and the kernel runs on (no trap).  In the normal build HPR_COL is the
+// index itself.
+#ifdef HPR_BOUNDS_CHECK
+__device__ unsigned long long g_bounds_violations = 0;
+__device__ __forceinline__ int col_checked(int c, int len)
+{
+    if ((unsigned)c >= (unsigned)len) {
+        atomicAdd(&g_bounds_violations, 1ull);
+        return 0;
+    }
+    return c;
+}
+#define HPR_COL(c, len) ::hprdev::col_checked((c), (len))
+#else
+#define HPR_COL(c, len) (c)
+#endif
+
 constexpr int TB = 256;                 // threads per CTA (vector, reduction kernels)
 #ifndef HPR_SELL_TB
 #define HPR_SELL_TB 64
@@ -226,6 +246,7 @@ struct SellArgs {
     const int *wstart;    // nruns + 1: unit i covers slices [wstart[i], wstart[i+1])
     const void *val;      // stored values, double or float (E::Val); padding: 0
     const int *col;       // stored column indices (padding: 0)
+    int cols;             // length of the gathered vectors (columns of the matrix)
     const int *skip;      // optional: the kernel does nothing while *skip != 0
     int trigger_from;     // programmatic launch: CTAs from this index on let the next kernel
                           // start once they have waited for the previous one (others: at exit)
@@ -292,7 +313,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 v[u] = __ldcs(pv + (k + u) * 32);
-                c[u] = __ldcs(pc + (k + u) * 32);
+                c[u] = HPR_COL(__ldcs(pc + (k + u) * 32), S.cols);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -318,7 +339,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
                 v[u] = u < rem ? __ldcs(pv + (k + u) * 32) : V(0);
-                c[u] = u < rem ? __ldcs(pc + (k + u) * 32) : 0;
+                c[u] = u < rem ? HPR_COL(__ldcs(pc + (k + u) * 32), S.cols) : 0;
             }
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
@@ -335,7 +356,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
         } else {
             for (; k < steps; ++k) {
                 const V v = __ldcs(pv + k * 32);
-                const int c = __ldcs(pc + k * 32);
+                const int c = HPR_COL(__ldcs(pc + k * 32), S.cols);
                 a0.add(v, __ldg(ee.xa + c));
                 if (NV == 2) b0.add(v, __ldg(ee.xb + c));
             }
@@ -1004,12 +1025,12 @@ __global__ void k_unpermute(int64_t len, const double *__restrict__ src, const i
 }
 
 // stored values of a sliced-ELL matrix from the CSR values (-1: padding, value 0)
-__global__ void k_gather_src(int64_t len, const double *__restrict__ csr, const int *__restrict__ src,
+__global__ void k_gather_src(int64_t len, const double *__restrict__ csr, int csr_len, const int *__restrict__ src,
                              double *dst)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
         const int p = src[i];
-        dst[i] = p >= 0 ? csr[p] : 0.0;
+        dst[i] = p >= 0 ? csr[HPR_COL(p, csr_len)] : 0.0;
     }
 }
 
@@ -1092,7 +1113,7 @@ __global__ void k_gather(int64_t nnz, const double *__restrict__ src, const int 
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
          k += (int64_t)gridDim.x * blockDim.x)
-        dst[k] = src[perm[k]];
+        dst[k] = src[HPR_COL(perm[k], (int)nnz)];
 }
 
 // d_i = max_p |val_p| over row i, in index order
@@ -1134,13 +1155,13 @@ __global__ void k_factor(int rows, double *d, double *D)
 }
 
 // a_ij <- a_ij * dr_i * dc_j
-__global__ void k_scale_rows_cols(int rows, const int *__restrict__ rp, const int *__restrict__ ci,
+__global__ void k_scale_rows_cols(int rows, int cols, const int *__restrict__ rp, const int *__restrict__ ci,
                                   double *val, const double *__restrict__ dr,
                                   const double *__restrict__ dc)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
         const double r = dr[i];
-        for (int p = rp[i]; p < rp[i + 1]; ++p) val[p] = val[p] * r * dc[ci[p]];
+        for (int p = rp[i]; p < rp[i + 1]; ++p) val[p] = val[p] * r * dc[HPR_COL(ci[p], cols)];
     }
 }
 

@@ -141,13 +141,13 @@ __device__ __forceinline__ void grid_rows(const hprsmall::SmallMat &M, const dou
         for (; k + 1 < steps; k += 2) {
             const int pa = p0 + (k << 5), pb = pa + 32;
             const double va = __ldg(M.val + pa), vb = __ldg(M.val + pb);
-            const int ca = __ldg(M.col + pa), cb = __ldg(M.col + pb);
+            const int ca = HPR_COL(__ldg(M.col + pa), M.cols), cb = HPR_COL(__ldg(M.col + pb), M.cols);
             a0 = fma(va, __ldcg(x + ca), a0);
             a1 = fma(vb, __ldcg(x + cb), a1);
         }
         if (k < steps) {
             const int pa = p0 + (k << 5);
-            a0 = fma(__ldg(M.val + pa), __ldcg(x + __ldg(M.col + pa)), a0);
+            a0 = fma(__ldg(M.val + pa), __ldcg(x + HPR_COL(__ldg(M.col + pa), M.cols)), a0);
         }
         double sum = steps > 1 ? a0 + a1 : a0;
         for (int o = 1; o < (1 << lg); o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);

@@ -27,6 +27,7 @@ constexpr int NW = NT / 32;
 // L = 2^slg[s] lanes per row, entries sptr[s] .. sptr[s+1]-1 in steps of 32, column-major)
 struct SmallMat {
     int nslices;
+    int cols;                                // length of the gathered vectors
     int64_t entries;
     const int *srow, *sptr, *col;
     const unsigned char *slg;
@@ -86,12 +87,12 @@ __device__ __forceinline__ void sell_rows(const SmallMat &M, const double *x, F 
         int k = 0;
         for (; k + 1 < steps; k += 2) {
             const int pa = p0 + (k << 5), pb = pa + 32;
-            a0 = fma(M.val[pa], x[M.col[pa]], a0);
-            a1 = fma(M.val[pb], x[M.col[pb]], a1);
+            a0 = fma(M.val[pa], x[HPR_COL(M.col[pa], M.cols)], a0);
+            a1 = fma(M.val[pb], x[HPR_COL(M.col[pb], M.cols)], a1);
         }
         if (k < steps) {
             const int pa = p0 + (k << 5);
-            a0 = fma(M.val[pa], x[M.col[pa]], a0);
+            a0 = fma(M.val[pa], x[HPR_COL(M.col[pa], M.cols)], a0);
         }
         double sum = steps > 1 ? a0 + a1 : a0;
         for (int o = 1; o < (1 << lg); o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);

@@ -100,6 +100,7 @@ SIGNATURES = {
                                          ctypes.c_void_p, ctypes.c_void_p, _D, _I64]),
     "hpr_get_layout": (ctypes.c_int, [ctypes.c_void_p, _I64, _D, _I64]),
     "hpr_memory_probe": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, _D, _D]),
+    "hpr_bounds_violations": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
     "hpr_layout_plan": (ctypes.c_int, [ctypes.POINTER(hpr_csr), ctypes.c_int64, ctypes.c_double, _I64, _I64,
                                        _I64, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_uint8), _I32, _I32,
                                        _I32]),
@@ -280,6 +281,13 @@ def hpr_time_iteration(ctx, reps: int):
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().hpr_time_iteration(ctx, int(reps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), ctx)
     return a.value, b.value, c.value
+
+
+def bounds_violations() -> int:
+    """Out-of-range gather indices counted by the bounds-checking build (-1: normal build)."""
+    c = ctypes.c_int64()
+    _check(load().hpr_bounds_violations(ctypes.byref(c)), None)
+    return int(c.value)
 
 
 def memory_probe(read_bytes=72_000_000, gather_len=1 << 18, stream=None):

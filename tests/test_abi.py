@@ -1,6 +1,7 @@
 """The C-ABI library: builds, exports every symbol include/hpr.h declares, matches the
 header's struct layouts, and rejects bad input on the host (no GPU needed: validation
 runs before any device call)."""
+import ctypes
 import os
 import re
 import subprocess
@@ -161,3 +162,15 @@ def test_power_noalloc_rejects_sizes_beyond_its_bound(lib):
             hpr.hpr_power_noalloc(m, n, (1, 1, 1), (1, 1, 1), 0, 10, 1e-10, 1, 1)
         assert e.value.code == hpr.HPR_ERR_ARG
         assert "2^31 - 2" in hpr.hpr_last_error(None)
+
+
+def test_normal_build_checks_no_bounds(lib):
+    """The normal build counts nothing (-1) and needs no device to say so; the bounds-checking
+    build, when built, exports the same entry points."""
+    assert hpr.bounds_violations() == -1
+    from paper_2408_12179_b300 import build as solver_build
+    if not os.path.exists(solver_build.LIB_CHECKED):
+        pytest.skip("the bounds-checking build is not built")
+    checked = ctypes.CDLL(solver_build.LIB_CHECKED)
+    for name in declared_functions():
+        getattr(checked, name)
