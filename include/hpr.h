@@ -230,6 +230,29 @@ int hpr_solve(hpr_ctx *ctx, double tol);
  * into *info; any pointer may be NULL.  HPR_ERR_STATE before the first solve. */
 int hpr_get(const hpr_ctx *ctx, double *x, double *y, double *z, hpr_info *info);
 
+/* ---- Checkpoint / resume (no counterpart in the paper; its natural checkpoint is the
+ * restart state of Algorithm 2: the anchor w^{r,0} = w_bar^{r-1,tau}, sigma_r, the
+ * counters r and k at the restart, with lambda and the scaling).
+ * hpr_get_state writes the state of the last restart of the last hpr_solve (the origin
+ * and sigma_0 if it made none) into a caller buffer: an opaque blob of
+ * hpr_get_state(ctx, NULL, 0, &bytes) bytes, in the solver's internal (scaled, renumbered)
+ * order, valid for a context of the same LP with the same options.  hpr_set_state loads
+ * such a blob; the next hpr_solve of that context then starts from it -- no power method
+ * (lambda is the blob's), the restart step of Algorithm 2 applied to the stored anchor,
+ * the counters continued -- and runs on the multi-CTA path.  Since a solve stopped by
+ * max_iter takes no restart decision at its last check, resuming from its state replays
+ * the uninterrupted solve bit for bit (same iterations, same w_bar).
+ *   hpr_get_state: HPR_ERR_STATE before a solve, or when the last solve ran on a
+ *                  persistent path (persistent = 2, 3, 4, or 1 when it chose one: its
+ *                  anchors live in shared memory; solve with persistent = 0 to checkpoint);
+ *                  HPR_ERR_ARG when buf is non-NULL and bytes is smaller than needed.
+ *   hpr_set_state: HPR_ERR_ARG when the blob is shorter than needed, or was taken from
+ *                  another LP (sizes or scaling differ) or another build of the blob;
+ *                  HPR_ERR_STATE for a context in a batch, with tracing or a sigma
+ *                  policy (their history is not part of the state). */
+int hpr_get_state(const hpr_ctx *ctx, void *buf, int64_t bytes, int64_t *needed);
+int hpr_set_state(hpr_ctx *ctx, const void *buf, int64_t bytes);
+
 /* Preprocessing results: D_r (m), D_c (n), the scaled values of A in the CSR order of
  * [A1; A2] (nnz), the scaled b (m), c, l, u (n) and beta = {||D_r b||+1, ||D_c c||+1}
  * (2).  Any pointer may be NULL. */

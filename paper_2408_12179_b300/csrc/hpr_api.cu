@@ -96,7 +96,23 @@ struct SolveState {
     double policy_kkt = 0.0;              // KKT residual at the learned decision
     int L = 0;                            // the current period: iterations and whether it
     bool first_r0 = false;                // starts an inner loop (t = 0)
+    // the last restart (the checkpoint of hpr_get_state): its iteration count, sigma and
+    // form; the anchors x0, y0 keep its w_bar for the whole inner loop
+    int64_t k_restart = 0;
+    double sigma_restart = 1.0;
+    int form_restart = 0;
 };
+
+// header of a checkpoint blob (hpr_get_state / hpr_set_state), followed by the anchors
+// x0 (n doubles) and y0 (m doubles) in the internal (scaled, renumbered) order
+struct StateHdr {
+    uint64_t magic;
+    int64_t n, m, m1, nnz, precision, check_every;
+    double beta_b, beta_c, norm_b, norm_c;   // the scaled LP's fingerprint
+    int64_t k, r, form, power_iters;
+    double sigma, lambda, power_rel_change;
+};
+constexpr uint64_t STATE_MAGIC = 0x4850525354415401ull;   // "HPRSTAT" and the layout version 1
 
 struct hpr_ctx {
     int device = 0;
@@ -191,6 +207,9 @@ struct hpr_ctx {
     hprgrid::GridBar *grid_bar = nullptr;
     int grid_ctas_used = 0;                   // CTAs of the last persistent grid or cluster solve
     int path_used = 0;                        // the path of the last solve (hpr_info.path)
+    bool resume_pending = false;              // hpr_set_state: the next solve starts from it
+    StateHdr resume_hdr{};
+    std::vector<double> resume_x0, resume_y0;
     int64_t grid_ctas_env = 0;                // HPR_GRID_CTAS: CTA count of that path (0: by size)
     int64_t fault_barrier = 0;                // HPR_FAULT_BARRIER=n: a CTA skips barrier n-1
     bool batched = false;         // owned by a batch: solved only through hpr_batch_solve

@@ -93,8 +93,15 @@ int solve_begin(hpr_ctx *ctx, double tol)
     S.t0 = now_s();
     ctx->launches = 0;
 
-    // ---- T1 = lambda I - A A^*: power method (counted in the solve time, Section 4.1)
-    if (o.lambda_fixed > 0.0) {
+    // ---- T1 = lambda I - A A^*: power method (counted in the solve time, Section 4.1);
+    // a resumed solve takes the checkpoint's lambda
+    const bool resume = ctx->resume_pending;
+    if (resume) {
+        ctx->lambda = ctx->resume_hdr.lambda;
+        ctx->power_iters = ctx->resume_hdr.power_iters;
+        ctx->power_time = 0.0;
+        ctx->power_rel_change = ctx->resume_hdr.power_rel_change;
+    } else if (o.lambda_fixed > 0.0) {
         ctx->lambda = o.lambda_fixed;
         ctx->power_iters = 0;
         ctx->power_time = 0.0;
@@ -118,8 +125,32 @@ int solve_begin(hpr_ctx *ctx, double tol)
     ctx->form = (int)o.precision;
     S.sigma = o.sigma0;
     S.status = HPR_MAX_ITER;
+    if (resume) {
+        // the checkpoint: Algorithm 2's restart step applied to its anchor, its sigma and
+        // counters (t = 0: a new inner loop)
+        const StateHdr &H = ctx->resume_hdr;
+        CK(cudaMemcpyAsync(ctx->xbar, ctx->resume_x0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->ybar, ctx->resume_y0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+        ctx->form = (int)H.form;
+        if (ctx->form == 1)
+            k_restart32<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->xbar, ctx->ybar, ctx->x32, ctx->x0,
+                                                        ctx->y32, ctx->y0, ctx->x032, ctx->y032);
+        else
+            k_restart<<<grid_for(n + m), 256, 0, s>>>((int)n, (int)m, ctx->xbar, ctx->ybar, ctx->x, ctx->x0,
+                                                      ctx->y, ctx->y0);
+        CKL();
+        ctx->launches += 1;
+        CK(cudaStreamSynchronize(s));
+        S.k = H.k;
+        S.r = H.r;
+        S.sigma = H.sigma;
+        ctx->resume_pending = false;
+    }
+    S.k_restart = S.k;
+    S.sigma_restart = S.sigma;
+    S.form_restart = ctx->form;
     S.tracing = ctx->trace_n > 0;
-    S.done = o.max_iter <= 0;
+    S.done = o.max_iter <= S.k;
     return HPR_OK;
 }
 
@@ -353,6 +384,9 @@ int period_after(hpr_ctx *ctx, double elapsed)
         S.sigma = sigma_next;
         S.t = 0;
         S.r++;
+        S.k_restart = kk + 1;                // the checkpoint: this restart
+        S.sigma_restart = S.sigma;
+        S.form_restart = ctx->form;
     } else {
         S.t = tl + 1;
     }
@@ -429,6 +463,7 @@ double small_fp64_per_iter(const hpr_ctx *ctx)
 const char *small_unfit(const hpr_ctx *ctx, bool forced)
 {
     const hpr_options &o = ctx->opt;
+    if (ctx->resume_pending) return "a pending resume (hpr_set_state)";
     if (hprsmall::small_vec_bytes((int)ctx->m, (int)ctx->n) > SMALL_SMEM_MAX)
         return "the iterates do not fit in shared memory";
     if (o.precision != 0) return "the FP32 form";
@@ -577,6 +612,7 @@ constexpr double CLUSTER_WORK_MAX = 10500.0;
 const char *grid_unfit(const hpr_ctx *ctx, bool forced)
 {
     const hpr_options &o = ctx->opt;
+    if (ctx->resume_pending) return "a pending resume (hpr_set_state)";
     if (o.precision != 0) return "the FP32 form";
     if (o.trace_iters > 0) return "tracing";
     if (o.time_limit_s > 0.0) return "a time limit";
@@ -836,6 +872,67 @@ int hpr_get(const hpr_ctx *cctx, double *x, double *y, double *z, hpr_info *info
     if (z) CK(cudaMemcpyAsync(z, ctx->zo, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (info) *info = ctx->info;
+    return HPR_OK;
+}
+
+int hpr_get_state(const hpr_ctx *cctx, void *buf, int64_t bytes, int64_t *needed)
+{
+    if (!cctx) return HPR_ERR_ARG;
+    hpr_ctx *ctx = const_cast<hpr_ctx *>(cctx);
+    const int64_t n = ctx->n, m = ctx->m;
+    const int64_t need = (int64_t)sizeof(StateHdr) + (int64_t)sizeof(double) * (n + m);
+    if (needed) *needed = need;
+    if (!buf) return HPR_OK;
+    if (!ctx->solved) return fail_arg(ctx, HPR_ERR_STATE, "hpr_get_state: no solve has completed");
+    if (ctx->path_used != 0)
+        return fail_arg(ctx, HPR_ERR_STATE,
+                        "hpr_get_state: the last solve ran on a persistent path (its anchors stay in shared "
+                        "memory); solve with persistent = 0 to take a checkpoint");
+    if (bytes < need) return fail_arg(ctx, HPR_ERR_ARG, "hpr_get_state: the buffer is smaller than needed");
+    cudaSetDevice(ctx->device);
+    const SolveState &S = ctx->ss;
+    StateHdr H{};
+    H.magic = STATE_MAGIC;
+    H.n = n; H.m = m; H.m1 = ctx->m1; H.nnz = ctx->nnz;
+    H.precision = ctx->opt.precision; H.check_every = ctx->opt.check_every;
+    H.beta_b = ctx->beta_b; H.beta_c = ctx->beta_c; H.norm_b = ctx->norm_b; H.norm_c = ctx->norm_c;
+    H.k = S.k_restart; H.r = S.r; H.form = S.form_restart; H.power_iters = ctx->power_iters;
+    H.sigma = S.sigma_restart; H.lambda = S.lambda; H.power_rel_change = ctx->power_rel_change;
+    char *out = static_cast<char *>(buf);
+    memcpy(out, &H, sizeof H);
+    double *x0 = reinterpret_cast<double *>(out + sizeof H);
+    CK(cudaMemcpyAsync(x0, ctx->x0, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(x0 + n, ctx->y0, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return HPR_OK;
+}
+
+int hpr_set_state(hpr_ctx *ctx, const void *buf, int64_t bytes)
+{
+    if (!ctx) return HPR_ERR_ARG;
+    if (!buf) return fail_arg(ctx, HPR_ERR_ARG, "hpr_set_state: buf is NULL");
+    if (ctx->batched) return fail_arg(ctx, HPR_ERR_STATE, "hpr_set_state: the context belongs to a batch");
+    if (ctx->opt.trace_iters > 0 || ctx->opt.sigma_policy != 0)
+        return fail_arg(ctx, HPR_ERR_STATE, "hpr_set_state: tracing and a sigma policy cannot resume");
+    const int64_t n = ctx->n, m = ctx->m;
+    const int64_t need = (int64_t)sizeof(StateHdr) + (int64_t)sizeof(double) * (n + m);
+    if (bytes < (int64_t)sizeof(StateHdr) || bytes < need)
+        return fail_arg(ctx, HPR_ERR_ARG, "hpr_set_state: the blob is shorter than this LP's state");
+    StateHdr H;
+    memcpy(&H, buf, sizeof H);
+    if (H.magic != STATE_MAGIC) return fail_arg(ctx, HPR_ERR_ARG, "hpr_set_state: not a state blob of this build");
+    if (H.n != n || H.m != m || H.m1 != ctx->m1 || H.nnz != ctx->nnz || H.beta_b != ctx->beta_b ||
+        H.beta_c != ctx->beta_c || H.norm_b != ctx->norm_b || H.norm_c != ctx->norm_c)
+        return fail_arg(ctx, HPR_ERR_ARG, "hpr_set_state: the state was taken from another LP");
+    if (H.precision != ctx->opt.precision || H.check_every != ctx->opt.check_every)
+        return fail_arg(ctx, HPR_ERR_ARG, "hpr_set_state: the state was taken with another precision or check_every");
+    if (!(H.lambda > 0.0) || !(H.sigma > 0.0) || H.k < 0 || H.r < 0 || H.form < 0 || H.form > 1)
+        return fail_arg(ctx, HPR_ERR_ARG, "hpr_set_state: inconsistent state");
+    const double *x0 = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof H);
+    ctx->resume_x0.assign(x0, x0 + n);
+    ctx->resume_y0.assign(x0 + n, x0 + n + m);
+    ctx->resume_hdr = H;
+    ctx->resume_pending = true;
     return HPR_OK;
 }
 

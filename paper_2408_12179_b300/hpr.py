@@ -88,6 +88,8 @@ SIGNATURES = {
     "hpr_power": (ctypes.c_int, [ctypes.c_void_p, _D, _I64]),
     "hpr_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "hpr_get": (ctypes.c_int, [ctypes.c_void_p, _D, _D, _D, ctypes.POINTER(hpr_info)]),
+    "hpr_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "hpr_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "hpr_get_scaling": (ctypes.c_int, [ctypes.c_void_p, _D, _D, _D, _D, _D, _D, _D, _D]),
     "hpr_get_checks": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hpr_check_record),
                                       ctypes.c_int64, _I64]),
@@ -394,6 +396,18 @@ class Solver:
 
     def trace(self, k):
         return hpr_get_trace(self.ctx, k, self.n, self.m)
+
+    def get_state(self) -> bytes:
+        """The checkpoint of the last solve (hpr_get_state): an opaque blob."""
+        need = ctypes.c_int64()
+        _check(load().hpr_get_state(self.ctx, None, 0, ctypes.byref(need)), self.ctx)
+        buf = ctypes.create_string_buffer(need.value)
+        _check(load().hpr_get_state(self.ctx, buf, need.value, ctypes.byref(need)), self.ctx)
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        """The next solve starts from this checkpoint (hpr_set_state)."""
+        _check(load().hpr_set_state(self.ctx, blob, len(blob)), self.ctx)
 
     def result(self):
         """(x, y, z, info) of the last solve (e.g. one run through a Batch)."""
