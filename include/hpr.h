@@ -163,6 +163,29 @@ typedef struct {
     int64_t pdl;              /* 1 (default): the two phases of a normal iteration are launched as
                                  programmatic dependents of the kernel before them, so that their
                                  set-up overlaps its tail; 0: plain stream order */
+    int64_t gather_tiles;     /* the x phase of normal FP64 iterations on the multi-CTA path:
+                                 0 (default): the sliced-ELL kernel, which gathers y from L2;
+                                 1: gather-tiled when the x phase moves at least 40 MB (12 nnz +
+                                 60 n + 8 m bytes) and y takes at most one block per 4 SMs;
+                                 2: gather-tiled whenever y takes at most one block per SM
+                                 (HPR_ERR_ARG at hpr_create otherwise).  Gather-tiled: y is
+                                 cut into blocks of consecutive entries that fit one CTA's
+                                 shared memory, each CTA (one per SM) stages one block and
+                                 streams the entries of A^T whose columns lie in it, the
+                                 per-block partial sums of each row go to a buffer and a second
+                                 kernel adds them in block order before the x update.  Row
+                                 sums are added in another order than on the sliced-ELL
+                                 kernel (FP64 either way).  Decided at hpr_create (the layout
+                                 is built there); set to 0 later, the solve takes the
+                                 sliced-ELL kernel.  Check iterations, the FP32 form's normal
+                                 iterations, the persistent paths and batched solves always
+                                 take their own kernels.  On the medium planted LP (m = 200k,
+                                 n = 500k) the tiled x phase is slower (41 against 35 us): the
+                                 split adds FP64 work (per-block sums, a separate epilogue) on
+                                 B300's scarce FP64 pipe */
+    int64_t tile_len;         /* gather_tiles: most entries of y in one block, 0 (default: as
+                                 many as one CTA's shared memory holds, 28,928 on B300) or in
+                                 [2, 65,536]; odd values are taken one lower */
 } hpr_options;
 
 /* Result summary (original, unscaled problem). */
@@ -187,6 +210,9 @@ typedef struct {
                                      0 multi-CTA (launches per iteration), 2 single-CTA, 3 grid,
                                      4 cluster */
     int64_t path_ctas;            /* CTAs of the persistent grid or cluster launch (else 0) */
+    int64_t x_tiles;              /* blocks of y of the gather-tiled x phase that the multi-CTA
+                                     path's normal FP64 iterations took (0: the sliced-ELL x
+                                     phase; see hpr_options.gather_tiles) */
 } hpr_info;
 
 /* One evaluation of the restart / termination quantities.  kind: 1 = periodic check,

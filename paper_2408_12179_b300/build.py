@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "hpr_api.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", "hpr_device.cuh"), os.path.join(HERE, "csrc", "hpr_mlp.cuh"),
               os.path.join(HERE, "csrc", "hpr_small.cuh"), os.path.join(HERE, "csrc", "hpr_grid.cuh"),
-              os.path.join(HERE, "csrc", "hpr_cluster.cuh"),
+              os.path.join(HERE, "csrc", "hpr_cluster.cuh"), os.path.join(HERE, "csrc", "hpr_tiles.cuh"),
               *(os.path.join(HERE, "csrc", f"hpr_api_{part}.cuh") for part in ("solve", "batch", "policy", "noalloc", "probe")),
               os.path.join(ROOT, "include", "hpr.h")]
 LIB = os.path.join(HERE, "libhpr_b300.so")

@@ -26,6 +26,7 @@
 #include "hpr_small.cuh"
 #include "hpr_grid.cuh"
 #include "hpr_cluster.cuh"
+#include "hpr_tiles.cuh"
 
 #include <cuda_runtime.h>
 
@@ -79,6 +80,20 @@ struct SellDev {
     int *src = nullptr;           // CSR position of each stored entry (-1: padding)
 };
 
+// A^T in the gather-tiled layout of the x phase (device arrays; see k_tile_part)
+struct TileDev {
+    int nblk = 0;                 // blocks of y (0: the layout is not built)
+    int grid = 0;                 // CTAs of k_tile_part (one per SM)
+    int glen_max = 0;             // entries of the longest block (its shared memory / 8)
+    int64_t entries = 0, nsub = 0;   // stored entries (with padding); sub-rows = slots of P
+    int *cta_blk = nullptr, *bstart = nullptr, *ustart = nullptr, *wstart = nullptr;
+    int4 *smeta = nullptr;
+    int *oslot = nullptr, *slot_ptr = nullptr, *src = nullptr;
+    unsigned short *col = nullptr;
+    double *val = nullptr, *P = nullptr;
+    unsigned *ctr = nullptr;
+};
+
 // state of a solve between its periods (Algorithm 2's counters and the last check)
 struct SolveState {
     double tol = 1e-8, t0 = 0.0, lambda = 0.0, sigma = 1.0;
@@ -129,6 +144,7 @@ struct hpr_ctx {
     int *T_rp = nullptr, *T_ci = nullptr, *T_perm = nullptr;
     double *T_val = nullptr;
     SellDev SA, ST;               // A and A^T in the renumbered sliced-ELL layout
+    TileDev TX;                   // A^T in the gather-tiled layout (x phase), if built
     int *perm_r = nullptr;        // renumbered row i of A is original row perm_r[i]
     int *perm_c = nullptr;        // renumbered column j is original column perm_c[j]
     unsigned char *ineq = nullptr;// renumbered row i belongs to A2 (m2 block)
@@ -419,6 +435,198 @@ SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int 
     return h;
 }
 
+// Gather-tiled layout of a matrix whose phase gathers a vector of `cols` entries (see
+// k_tile_part): the gathered vector is cut into blocks of at most `tile_len` consecutive
+// entries (even, so every block starts 16-byte aligned), balanced by stored entries; each
+// block gets CTAs of the grid in proportion to its entries (at least one); the entries of
+// each block form a sub-matrix whose rows (sub-rows: the rows with an entry in the block,
+// in renumbered order) take the sliced-ELL layout of build_sell with column offsets within
+// the block.  Slot q of P holds a sub-row's sum; row r owns slots slot_ptr[r] ..
+// slot_ptr[r+1]-1, in block order.  A work unit is a run of consecutive slices of one block.
+// Rows are in the order perm, columns renamed by icol
+// (the renumbering of the sliced-ELL layout).  Returns false (layout not built) when the
+// blocks would outnumber the grid's CTAs or k_tile_epi's counter reset.
+// work units of the tiled layout: runs of slices of one block, each slice costing its steps
+// + 4; a block's units are sized so that each warp of its CTAs gets about TILE_UNITS_PER_WARP
+// of them (at least TILE_UNIT_MIN)
+constexpr int TILE_UNITS_PER_WARP = 4;
+constexpr int TILE_UNIT_MIN = 12;
+
+struct TileHost {
+    int nblk = 0;
+    std::vector<int> bstart, ustart, cta_blk, wstart, srow, sptr, oslot, slot_ptr, src;
+    std::vector<unsigned char> slg;
+    std::vector<int4> smeta;         // per slice: srow, sptr, steps, slg | sub-rows << 8
+    std::vector<unsigned short> col;
+    int glen_max = 0;
+};
+
+bool build_tiles(const std::vector<int> &rp, const std::vector<int> &ci, int rows,
+                 const std::vector<int> &perm, const std::vector<int> &icol, int cols,
+                 int tile_len, int grid, int steps_max, double unit_cost, TileHost &h)
+{
+    tile_len &= ~1;
+    if (rows < 1 || cols < 1 || tile_len < 2 || tile_len > 65536 || grid < 1) return false;
+    const int64_t nnz = rp[(size_t)rows];
+    std::vector<int64_t> cnt((size_t)cols, 0);
+    for (int64_t p = 0; p < nnz; ++p) cnt[(size_t)icol[(size_t)ci[(size_t)p]]]++;
+    // block boundaries: cut at an even column once the block holds its share of the
+    // entries, or at tile_len columns
+    const int goal = (int)std::min<int64_t>(grid, ((int64_t)cols + tile_len - 1) / tile_len);
+    h.bstart.assign(1, 0);
+    {
+        int64_t acc = 0;
+        int start = 0;
+        for (int c = 0; c < cols; ++c) {
+            if (c > start && (c & 1) == 0) {
+                const int b = (int)h.bstart.size() - 1;
+                const bool full = c - start >= tile_len;
+                const bool share = b + 1 < goal && (double)acc >= (double)nnz * (b + 1) / goal;
+                if (full || share) {
+                    h.bstart.push_back(c);
+                    start = c;
+                }
+            }
+            acc += cnt[(size_t)c];
+        }
+        h.bstart.push_back(cols);
+    }
+    const int nblk = (int)h.bstart.size() - 1;
+    if (nblk > grid || nblk > TILE_MAX_BLOCKS) return false;
+    h.nblk = nblk;
+    std::vector<int> colblk((size_t)cols);
+    std::vector<int64_t> bnnz((size_t)nblk, 0);
+    for (int b = 0; b < nblk; ++b) {
+        h.glen_max = std::max(h.glen_max, h.bstart[(size_t)b + 1] - h.bstart[(size_t)b]);
+        for (int c = h.bstart[(size_t)b]; c < h.bstart[(size_t)b + 1]; ++c) {
+            colblk[(size_t)c] = b;
+            bnnz[(size_t)b] += cnt[(size_t)c];
+        }
+    }
+    // CTAs per block: one each, the rest one at a time to the block with the most entries
+    // per CTA
+    std::vector<int> ncta((size_t)nblk, 1);
+    for (int g = nblk; g < grid; ++g) {
+        int best = 0;
+        for (int b = 1; b < nblk; ++b)
+            if ((double)bnnz[(size_t)b] / ncta[(size_t)b] > (double)bnnz[(size_t)best] / ncta[(size_t)best]) best = b;
+        ncta[(size_t)best]++;
+    }
+    h.cta_blk.clear();
+    for (int b = 0; b < nblk; ++b) h.cta_blk.insert(h.cta_blk.end(), (size_t)ncta[(size_t)b], b);
+    // the sub-matrices (CSR, rows in renumbered order) and the slots of each row
+    std::vector<std::vector<int>> brow((size_t)nblk), brp((size_t)nblk), bci((size_t)nblk), bpos((size_t)nblk);
+    for (int b = 0; b < nblk; ++b) {
+        bci[(size_t)b].reserve((size_t)bnnz[(size_t)b]);
+        bpos[(size_t)b].reserve((size_t)bnnz[(size_t)b]);
+    }
+    std::vector<int> last((size_t)nblk, -1);
+    h.slot_ptr.assign((size_t)rows + 1, 0);
+    for (int r = 0; r < rows; ++r) {
+        const int orow = perm[(size_t)r];
+        int nb = 0;
+        for (int p = rp[(size_t)orow]; p < rp[(size_t)orow + 1]; ++p) {
+            const int c = icol[(size_t)ci[(size_t)p]];
+            const int b = colblk[(size_t)c];
+            if (last[(size_t)b] != r) {
+                last[(size_t)b] = r;
+                brow[(size_t)b].push_back(r);
+                brp[(size_t)b].push_back((int)bci[(size_t)b].size());
+                ++nb;
+            }
+            bci[(size_t)b].push_back(c - h.bstart[(size_t)b]);
+            bpos[(size_t)b].push_back(p);
+        }
+        h.slot_ptr[(size_t)r + 1] = h.slot_ptr[(size_t)r] + nb;
+    }
+    for (int b = 0; b < nblk; ++b) brp[(size_t)b].push_back((int)bci[(size_t)b].size());
+    // slot of each sub-row: its row's slots are taken in block order
+    std::vector<std::vector<int>> bslot((size_t)nblk);
+    {
+        std::vector<int> fill(h.slot_ptr.begin(), h.slot_ptr.end() - 1);
+        for (int b = 0; b < nblk; ++b) {
+            bslot[(size_t)b].resize(brow[(size_t)b].size());
+            for (size_t q = 0; q < brow[(size_t)b].size(); ++q)
+                bslot[(size_t)b][q] = fill[(size_t)brow[(size_t)b][q]]++;
+        }
+    }
+    // sliced ELL of each sub-matrix (blocks in parallel on up to 16 host threads)
+    std::vector<SellHost> bh((size_t)nblk);
+    std::vector<std::vector<int>> bperm((size_t)nblk);
+    auto lay = [&](int b) {
+        const int nr = (int)brow[(size_t)b].size();
+        const int len = h.bstart[(size_t)b + 1] - h.bstart[(size_t)b];
+        std::vector<int> ident((size_t)len);
+        for (int c = 0; c < len; ++c) ident[(size_t)c] = c;
+        bperm[(size_t)b] = order_by_length(brp[(size_t)b], nr);
+        bh[(size_t)b] = build_sell(brp[(size_t)b], bci[(size_t)b], nr, bperm[(size_t)b], ident, steps_max, unit_cost);
+    };
+    {
+        const int nthr = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (int t = 0; t < std::min(nthr, nblk); ++t)
+            pool.emplace_back([&, t] {
+                for (int b = t; b < nblk; b += nthr) lay(b);
+            });
+        for (auto &th : pool) th.join();
+    }
+    // concatenation: slices, entries, sub-rows and units of block b follow those of b - 1
+    h.ustart.assign(1, 0);
+    h.wstart.clear();
+    h.smeta.clear();
+    h.srow.assign(1, 0);
+    h.sptr.assign(1, 0);
+    h.slg.clear();
+    h.oslot.clear();
+    h.col.clear();
+    h.src.clear();
+    int slice0 = 0, sub0 = 0, ent0 = 0;
+    for (int b = 0; b < nblk; ++b) {
+        const SellHost &H = bh[(size_t)b];
+        int64_t total = 0;
+        for (int sl = 0; sl < H.nslices; ++sl) total += ((H.sptr[(size_t)sl + 1] - H.sptr[(size_t)sl]) >> 5) + 4;
+        const int64_t warps = (int64_t)ncta[(size_t)b] * (TILE_TB / 32) * TILE_UNITS_PER_WARP;
+        const int64_t unit_target = std::max<int64_t>(TILE_UNIT_MIN, (total + warps - 1) / warps);
+        int units = 0;
+        int64_t cost = 0;
+        for (int sl = 0; sl < H.nslices; ++sl) {
+            if (cost == 0) {
+                h.wstart.push_back(slice0 + sl);
+                ++units;
+            }
+            const int steps = (H.sptr[(size_t)sl + 1] - H.sptr[(size_t)sl]) >> 5;
+            cost += steps + 4;
+            if (cost >= unit_target) cost = 0;
+            h.smeta.push_back(make_int4(sub0 + H.srow[(size_t)sl], ent0 + H.sptr[(size_t)sl], steps,
+                                        (int)H.slg[(size_t)sl] | ((H.srow[(size_t)sl + 1] - H.srow[(size_t)sl]) << 8)));
+            h.srow.push_back(sub0 + H.srow[(size_t)sl + 1]);
+            h.sptr.push_back(ent0 + H.sptr[(size_t)sl + 1]);
+            h.slg.push_back(H.slg[(size_t)sl]);
+        }
+        h.ustart.push_back(h.ustart.back() + units);
+        for (size_t t = 0; t < brow[(size_t)b].size(); ++t)
+            h.oslot.push_back(bslot[(size_t)b][(size_t)bperm[(size_t)b][t]]);
+        for (size_t e = 0; e < H.col.size(); ++e) {
+            h.col.push_back((unsigned short)H.col[e]);
+            h.src.push_back(H.src[e] < 0 ? -1 : bpos[(size_t)b][(size_t)H.src[e]]);
+        }
+        slice0 += H.nslices;
+        sub0 += (int)brow[(size_t)b].size();
+        ent0 += (int)H.col.size();
+    }
+    h.wstart.push_back(slice0);
+    return true;
+}
+
+void free_tiles(TileDev &T)
+{
+    void *p[] = {T.cta_blk, T.bstart, T.ustart, T.wstart, T.smeta, T.oslot, T.slot_ptr, T.src,
+                 T.col, T.val, T.P, T.ctr};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    T = TileDev{};
+}
+
 int validate_block(hpr_ctx *ctx, const hpr_csr *B, const char *name, int64_t *rows, int64_t *cols)
 {
     if (!B || B->rows == 0) {
@@ -474,6 +682,7 @@ void free_all(hpr_ctx *c)
                    c->grid_partials, c->grid_bar, c->pow_ticket};
     for (void *p : dev)
         if (p) cudaFree(p);
+    free_tiles(c->TX);
     if (c->scal_h) cudaFreeHost(c->scal_h);
     if (c->ctl_h) cudaFreeHost(c->ctl_h);
     if (c->pctl_h) cudaFreeHost(c->pctl_h);
@@ -637,9 +846,47 @@ EpiPrimal epi_primal(hpr_ctx *ctx)
 
 // the two phases of a normal iteration, as a solve launches them (programmatic dependent
 // launches)
+// the x phase of a normal FP64 iteration on the gather-tiled layout: k_tile_part (y in
+// shared memory, partial sums) then k_tile_epi (the sums and the x update), both launched
+// as programmatic dependents like the sliced-ELL phases
+int launch_tiles_x(hpr_ctx *ctx, int it)
+{
+    const TileDev &T = ctx->TX;
+    TileArgs a{};
+    a.cta_blk = T.cta_blk; a.bstart = T.bstart; a.ustart = T.ustart; a.wstart = T.wstart;
+    a.smeta = T.smeta; a.oslot = T.oslot; a.val = T.val; a.col = T.col;
+    a.P = T.P; a.ctr = T.ctr; a.g = ctx->y;
+    a.trigger_from = 0;                          // one CTA per SM: a single wave
+    TileEpiArgs b{};
+    b.rows = (int)ctx->n; b.nblk = T.nblk; b.slot_ptr = T.slot_ptr; b.P = T.P; b.ctr = T.ctr;
+    const int ge = (int)((ctx->n + TB - 1) / TB);
+    b.trigger_from = std::max(0, ge - (2048 / TB) * ctx->num_sms);
+    const EpiX<false> e = epi_x<false>(ctx, it);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.stream = ctx->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = ctx->opt.pdl ? 1 : 0;
+    cfg.gridDim = dim3((unsigned)T.grid);
+    cfg.blockDim = dim3(TILE_TB);
+    cfg.dynamicSmemBytes = sizeof(double) * (size_t)T.glen_max;
+    CK(cudaLaunchKernelEx(&cfg, k_tile_part, a));
+    cfg.gridDim = dim3((unsigned)ge);
+    cfg.blockDim = dim3(TB);
+    cfg.dynamicSmemBytes = 0;
+    CK(cudaLaunchKernelEx(&cfg, k_tile_epi<EpiX<false>>, b, e));
+    ctx->launches += 2;
+    return HPR_OK;
+}
+
+bool tiles_on(const hpr_ctx *ctx) { return ctx->TX.nblk > 0 && ctx->opt.gather_tiles != 0; }
+
 int launch_normal_x(hpr_ctx *ctx, int it)
 {
     if (ctx->form == 1) return launch_sell_pdl(ctx, ctx->ST, epi_x32<false>(ctx, it));
+    if (tiles_on(ctx)) return launch_tiles_x(ctx, it);
     return launch_sell_pdl(ctx, ctx->ST, epi_x<false>(ctx, it));
 }
 
@@ -914,6 +1161,45 @@ int install_layout(hpr_ctx *ctx, SellDev &D, const SellHost &H, int rows, const 
     return HPR_OK;
 }
 
+// device copy of a gather-tiled layout (values gathered later from the scaled CSR values
+// through `src`, see tile_values)
+int upload_tiles(hpr_ctx *ctx, TileDev &T, const TileHost &H, int rows)
+{
+    cudaStream_t s = ctx->stream;
+    T.nblk = H.nblk;
+    T.grid = (int)H.cta_blk.size();
+    T.glen_max = H.glen_max;
+    T.entries = (int64_t)H.col.size();
+    T.nsub = (int64_t)H.oslot.size();
+    auto up = [&](auto *&d, const auto &v) -> int {
+        using E = typename std::remove_reference<decltype(v)>::type::value_type;
+        DALLOC(d, (int64_t)std::max<size_t>(v.size(), 1));
+        if (!v.empty()) CK(cudaMemcpyAsync(d, v.data(), sizeof(E) * v.size(), cudaMemcpyHostToDevice, s));
+        return HPR_OK;
+    };
+    int st;
+    if ((st = up(T.cta_blk, H.cta_blk)) || (st = up(T.bstart, H.bstart)) || (st = up(T.ustart, H.ustart)) ||
+        (st = up(T.wstart, H.wstart)) || (st = up(T.smeta, H.smeta)) ||
+        (st = up(T.oslot, H.oslot)) || (st = up(T.slot_ptr, H.slot_ptr)) || (st = up(T.src, H.src)) ||
+        (st = up(T.col, H.col)))
+        return st;
+    DALLOC(T.val, std::max<int64_t>(T.entries, 1));
+    DALLOC(T.P, std::max<int64_t>(T.nsub, 1));
+    DALLOC(T.ctr, T.nblk);
+    CK(cudaMemsetAsync(T.ctr, 0, sizeof(unsigned) * T.nblk, s));
+    (void)rows;
+    return HPR_OK;
+}
+
+// the tiled layout's values from the scaled CSR values of A^T
+int tile_values(hpr_ctx *ctx, TileDev &T)
+{
+    if (!T.nblk || !T.entries) return HPR_OK;
+    k_gather_src<<<grid_for(T.entries), 256, 0, ctx->stream>>>(T.entries, ctx->T_val, (int)ctx->nnz, T.src, T.val);
+    CKL();
+    return HPR_OK;
+}
+
 // average duration (ms) of a plain phase launch with the current layout: 2 launches to
 // warm up, then 5 back to back between CUDA events (the values do not change the timing)
 int time_phase(hpr_ctx *ctx, bool transpose, double *ms)
@@ -1061,6 +1347,22 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     const double costT = op.unit_cost_t > 0.0 ? op.unit_cost_t : (smallT ? SMALL_UNIT_COST : UNIT_COST);
     SellHost hA = build_sell(rp, ci, (int)m, pr, ipc, stepsA, costA);
     SellHost hT = build_sell(trp, tci, (int)n, pc, ipr, stepsT, costT);
+    // the gather-tiled x phase (k_tile_part): y in blocks of shared memory
+    TileHost hX;
+    bool tiles = false;
+    if (op.gather_tiles != 0) {
+        int smem = 0;
+        CK(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        const int cap = std::min(65536, (smem - 1024) / 8) & ~1;
+        const int len = op.tile_len > 0 ? (int)std::min<int64_t>(op.tile_len, cap) : cap;
+        // option 1: a phase that moves enough data to be bound by its gathers, with at least
+        // 4 CTAs per block of y
+        const bool want = op.gather_tiles == 2 ||
+                          (!smallT && (m + len - 1) / len <= ctx->num_sms / 4);
+        if (want) tiles = build_tiles(trp, tci, (int)n, pc, ipr, (int)m, len, ctx->num_sms, stepsT, costT, hX);
+        if (!tiles && op.gather_tiles == 2)
+            return fail_arg(ctx, HPR_ERR_ARG, "gather_tiles = 2: y needs more blocks than the GPU has SMs");
+    }
     std::vector<unsigned char> ineq((size_t)m);
     for (int64_t i = 0; i < m; ++i) ineq[(size_t)i] = pr[(size_t)i] >= m1 ? 1 : 0;
     {
@@ -1109,6 +1411,11 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     DALLOC(ctx->T_rp, n + 1); DALLOC(ctx->T_ci, nnz); DALLOC(ctx->T_perm, nnz); DALLOC(ctx->T_val, nnz);
     if ((st0 = upload_sell(ctx->SA, hA, (int)m))) return st0;
     if ((st0 = upload_sell(ctx->ST, hT, (int)n))) return st0;
+    if (tiles) {
+        if ((st0 = upload_tiles(ctx, ctx->TX, hX, (int)n))) return st0;
+        CK(cudaFuncSetAttribute(k_tile_part, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(double) * ctx->TX.glen_max));
+    }
     DALLOC(ctx->perm_r, m); DALLOC(ctx->perm_c, n); DALLOC(ctx->ineq, m);
 
     DALLOC(ctx->bp, m); DALLOC(ctx->wrp, m); DALLOC(ctx->cp, n); DALLOC(ctx->lp, n); DALLOC(ctx->up, n);
@@ -1192,6 +1499,7 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
     // the iteration's copies: stored values through the position map, vectors renumbered
     k_gather_src<<<grid_for(ctx->SA.entries), 256, 0, s>>>(ctx->SA.entries, ctx->A_val, (int)ctx->nnz, ctx->SA.src, ctx->SA.val); CKL();
     k_gather_src<<<grid_for(ctx->ST.entries), 256, 0, s>>>(ctx->ST.entries, ctx->T_val, (int)ctx->nnz, ctx->ST.src, ctx->ST.val); CKL();
+    if ((st = tile_values(ctx, ctx->TX))) return st;
     k_narrow<<<grid_for(ctx->SA.entries), 256, 0, s>>>(ctx->SA.entries, ctx->SA.val, ctx->SA.val32); CKL();
     k_narrow<<<grid_for(ctx->ST.entries), 256, 0, s>>>(ctx->ST.entries, ctx->ST.val, ctx->ST.val32); CKL();
     k_permute<<<gm, 256, 0, s>>>(m, ctx->b_s, ctx->perm_r, ctx->bp); CKL();
@@ -1314,6 +1622,8 @@ int hpr_default_options(hpr_options *o)
     o->policy_margin = 0.0;
     o->persistent = 1;
     o->pdl = 1;
+    o->gather_tiles = 0;
+    o->tile_len = 0;
     return HPR_OK;
 }
 
@@ -1336,6 +1646,9 @@ static int check_options(hpr_ctx *ctx, const hpr_options *o)
     if (o->sigma_policy < 0 || o->sigma_policy > 2) return fail_arg(ctx, HPR_ERR_ARG, "sigma_policy must be 0, 1 or 2");
     if (o->persistent < 0 || o->persistent > 4) return fail_arg(ctx, HPR_ERR_ARG, "persistent must be 0, 1, 2, 3 or 4");
     if (o->pdl != 0 && o->pdl != 1) return fail_arg(ctx, HPR_ERR_ARG, "pdl must be 0 or 1");
+    if (o->gather_tiles < 0 || o->gather_tiles > 2) return fail_arg(ctx, HPR_ERR_ARG, "gather_tiles must be 0, 1 or 2");
+    if (o->tile_len < 0 || o->tile_len == 1 || o->tile_len > 65536)
+        return fail_arg(ctx, HPR_ERR_ARG, "tile_len must be 0 or in [2, 65536]");
     if (!(o->policy_margin >= 0.0) || o->policy_margin > 100.0)
         return fail_arg(ctx, HPR_ERR_ARG, "policy_margin must be in [0, 100]");
     if (o->sell_steps_a < 0 || o->sell_steps_a > 4096 || o->sell_steps_t < 0 || o->sell_steps_t > 4096)
@@ -1459,7 +1772,8 @@ int hpr_set_options(hpr_ctx *ctx, const hpr_options *opt)
     if (opt->seed != ctx->opt.seed || opt->power_tol != ctx->opt.power_tol ||
         opt->power_max_iter != ctx->opt.power_max_iter)
         ctx->have_power = false;
-    if (opt->reflect != ctx->opt.reflect) {   // captured graphs hold the kernels' arguments
+    if (opt->reflect != ctx->opt.reflect || (opt->gather_tiles != 0) != (ctx->opt.gather_tiles != 0)) {
+        // captured graphs hold the kernels and their arguments
         for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
         ctx->graphs.clear();
     }

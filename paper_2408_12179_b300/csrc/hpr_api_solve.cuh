@@ -434,6 +434,7 @@ int solve_finish(hpr_ctx *ctx)
     I.policy_fallbacks = S.policy_fallbacks;
     I.path = ctx->path_used;
     I.path_ctas = ctx->grid_ctas_used;
+    I.x_tiles = (ctx->path_used == 0 && !ctx->batched && tiles_on(ctx)) ? ctx->TX.nblk : 0;
     ctx->solved = true;
     return S.status;
 }

@@ -49,7 +49,8 @@ class hpr_options(ctypes.Structure):
                 ("sell_steps_t", ctypes.c_int64), ("unit_cost_a", ctypes.c_double),
                 ("unit_cost_t", ctypes.c_double), ("sigma_policy", ctypes.c_int64),
                 ("policy_seed", ctypes.c_uint64), ("policy_margin", ctypes.c_double),
-                ("persistent", ctypes.c_int64), ("pdl", ctypes.c_int64)]
+                ("persistent", ctypes.c_int64), ("pdl", ctypes.c_int64),
+                ("gather_tiles", ctypes.c_int64), ("tile_len", ctypes.c_int64)]
 
 
 class hpr_info(ctypes.Structure):
@@ -64,7 +65,8 @@ class hpr_info(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("status", ctypes.c_int64),
                 ("iters_fp32", ctypes.c_int64),
                 ("policy_decisions", ctypes.c_int64), ("policy_fallbacks", ctypes.c_int64),
-                ("power_rel_change", ctypes.c_double), ("path", ctypes.c_int64), ("path_ctas", ctypes.c_int64)]
+                ("power_rel_change", ctypes.c_double), ("path", ctypes.c_int64), ("path_ctas", ctypes.c_int64),
+                ("x_tiles", ctypes.c_int64)]
 
 
 class hpr_check_record(ctypes.Structure):
