@@ -162,6 +162,24 @@ VARIANTS = {
 }
 
 
+def fp64_per_launch(hpr, lp, layout, phase):
+    """FP64 warp instructions of one normal-iteration launch of a phase in the FP64 form,
+    counted from its sliced-ELL layout (hpr_layout_plan, the layout hpr_create builds): one
+    DFMA per 32 stored entries, one DADD merging the two FMA chains of a slice of 4 or more
+    steps, log2(lanes per row) DADDs of the row's lane butterfly per slice, and the epilogue's
+    five FP64 instructions (DADD, DFMA, DFMA, DMUL, DFMA) per work unit (each unit applies its
+    32-row buffer once)."""
+    import numpy as np
+
+    k = 1 if phase == "x" else 0
+    M = lp.A.T.tocsr() if phase == "x" else lp.A.tocsr()
+    L = hpr.layout_plan(M, int(layout["sell_steps"][k]), float(layout["unit_cost"][k]))
+    steps = np.diff(L["sptr"]) // 32
+    units = len(L["wstart"]) - 1
+    return int(L["sptr"][-1] // 32 + np.count_nonzero(steps >= 4) + int(L["slg"].astype(np.int64).sum())
+               + 5 * units)
+
+
 def bucket_of(lp):
     """Size bucket of the batch workload's per-bucket autotuning: floor(log2 nnz)."""
     return int(math.floor(math.log2(max(lp.nnz, 1))))
@@ -480,6 +498,21 @@ def run_ours(args):
     if (NCU_TRAFFIC["source_sha1"] == kernel_source_sha1() and args.workload == "medium" and args.scale == 1.0
             and args.seed == 0 and args.precision == 0 and args.variant == "hpr"):
         traffic = NCU_TRAFFIC.get(dom)          # captured on this workload only
+    # the phases' second bound: FP64 issue (one DFMA per stored entry on B300's FP64 pipe)
+    fp64 = None
+    if args.precision == 0 and not args.autotune:
+        f_peak = hpr.fp64_probe(stream.cuda_stream)
+        f_inst = fp64_per_launch(hpr, lp, layout, "x" if dom == "k_phase_x" else "y")
+        f_ach = f_inst / (dom_ms * 1e-3) / 1e9
+        f_ach_graph = f_inst / (dom_in_graph_ms * 1e-3) / 1e9
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        fp64 = {"bound": "alu", "unit": "G FP64 warp instructions/s", "instructions_per_launch": f_inst,
+                "achieved": f_ach, "peak": f_peak, "frac": f_ach / f_peak,
+                "in_graph_frac": f_ach_graph / f_peak,
+                "peak_source": "hpr_fp64_probe (independent DFMA chains, this run)",
+                "peak_nominal": sms * 2.032e9 / 16 / 1e9,
+                "peak_nominal_source": "one FP64 warp instruction per 16 cycles per SM at 2032 MHz "
+                                       "(ncu: the probe runs at 84% of it)"}
     iter_gbs = (bx + by) / (ms_it * 1e-3) / 1e9
     plain = None
     if args.compare_fp64 and args.precision != 0:
@@ -561,7 +594,8 @@ def run_ours(args):
                      "ceilings": ceil,
                      "frac_of_read_stream_same_size": achieved / ceil["read_gbs_phase_size"],
                      "gathers_per_launch": gathers, "gather_g_per_s": gather_rate,
-                     "frac_of_gather_rate": gather_rate / ceil["gather_g_per_s"]},
+                     "frac_of_gather_rate": gather_rate / ceil["gather_g_per_s"],
+                     "fp64": fp64},
         "gpu_launches": int(sum(i["launches"] for i in infos)),
         "e2e": e2e,
         "clocks": clocks,

@@ -361,6 +361,17 @@ int hpr_bounds_violations(int64_t *count);
 int hpr_memory_probe(int64_t read_bytes, int64_t gather_len, void *cuda_stream, double *read_gbs,
                      double *gather_gps);
 
+/* ---- FP64 issue probe (no counterpart in the paper: a measurement aid for the benchmark's
+ * roofline).  B300 issues FP64 at a small fraction of its FP32 rate, and every stored matrix
+ * entry of an HPR phase costs one DFMA: the phases are bound by FP64 issue as well as by HBM.
+ * Times a kernel of independent DFMA chains (eight per thread, 8 warps per CTA, 8 CTAs per
+ * SM) on the current device and writes the whole GPU's rate of FP64 warp instructions, in
+ * 1e9 per second, to *warp_ginst_per_s (best of three launches after a warm-up).
+ *   cuda_stream   stream to run on (NULL: the legacy default stream); the call synchronises it.
+ * Allocates and frees 64 bytes of device memory.  Returns HPR_OK, HPR_ERR_ARG (NULL output),
+ * HPR_ERR_NO_DEVICE or HPR_ERR_NOMEM / HPR_ERR_CUDA (detail in hpr_last_error(NULL)). */
+int hpr_fp64_probe(void *cuda_stream, double *warp_ginst_per_s);
+
 /* Layout of the context's sliced-ELL copies (no counterpart in the paper: a storage choice
  * of this library), after autotuning if asked: for A (index 0) and A^T (index 1) the
  * lanes-per-row bound, the work-unit size and the number of work units; any pointer may

@@ -58,6 +58,24 @@ __global__ void __launch_bounds__(256) k_probe_gather(const double *__restrict__
     if (acc == 0x9e3779b97f4a7c15ull) out[0] = acc;
 }
 
+// FP64 issue: eight independent DFMA chains per thread (a dependent DFMA takes ~70 cycles,
+// so a few warps per SM keep the FP64 pipe issuing every cycle it can)
+__global__ void __launch_bounds__(256) k_probe_fp64(int rounds, double *out)
+{
+    double a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = 1.0 + 1e-3 * (double)(threadIdx.x + 32 * u);
+    const double mul = 0.9999999999, add = 1e-12;
+    for (int r = 0; r < rounds; ++r) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = fma(a[u], mul, add);
+    }
+    double s = a[0];
+#pragma unroll
+    for (int u = 1; u < 8; ++u) s += a[u];
+    if (s == 1234.5678) out[0] = s;          // keeps the chains; practically never taken
+}
+
 __global__ void k_probe_fill(uint4 *p, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -152,5 +170,50 @@ extern "C" int hpr_memory_probe(int64_t read_bytes, int64_t gather_len, void *cu
     if (e1) cudaEventDestroy(e1);
     for (void *p : {(void *)buf, (void *)flush, (void *)gx, (void *)out})
         if (p) cudaFree(p);
+    return rc;
+}
+
+// FP64 warp instructions per second of the whole GPU (DFMA with all 32 lanes active)
+extern "C" int hpr_fp64_probe(void *cuda_stream, double *warp_ginst_per_s)
+{
+    if (!warp_ginst_per_s) {
+        g_static_err = "hpr_fp64_probe: warp_ginst_per_s is NULL";
+        return HPR_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        g_static_err = "hpr_fp64_probe: no CUDA device";
+        return HPR_ERR_NO_DEVICE;
+    }
+    double *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = HPR_OK;
+    auto ok = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == HPR_OK) {
+            rc = e == cudaErrorMemoryAllocation ? HPR_ERR_NOMEM : HPR_ERR_CUDA;
+            g_static_err = "hpr_fp64_probe: CUDA error";
+        }
+        return rc == HPR_OK;
+    };
+    const int rounds = 2048, grid = sms * 8;
+    float best = 1e30f;
+    if (ok(cudaMalloc((void **)&out, 64)) && ok(cudaEventCreate(&e0)) && ok(cudaEventCreate(&e1))) {
+        for (int r = 0; r < 4 && rc == HPR_OK; ++r) {
+            ok(cudaEventRecord(e0, s));
+            k_probe_fp64<<<grid, 256, 0, s>>>(rounds, out);
+            ok(cudaEventRecord(e1, s));
+            ok(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            ok(cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) best = std::min(best, ms);                           // the first run warms up
+        }
+        ok(cudaGetLastError());
+        if (rc == HPR_OK) *warp_ginst_per_s = (double)grid * (256 / 32) * rounds * 8 / (best * 1e-3) / 1e9;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) cudaFree(out);
     return rc;
 }

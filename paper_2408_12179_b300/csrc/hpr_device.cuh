@@ -332,7 +332,16 @@ __device__ __forceinline__ void sell_unit(const SellArgs &S, const E &ee, int ru
                 b1.add(v[3], g1[3]);
             }
         }
-        if (steps < 4) {                          // a short slice: its 1-3 steps as one batch
+        if (steps == 1) {                         // one step (most rows of A^T of a sparse LP)
+            const V v = __ldcs(pv + k * 32);
+            const int c = HPR_COL(__ldcs(pc + k * 32), S.cols);
+            const V g0 = __ldg(ee.xa + c);
+            if (NV == 2) {
+                const V g1 = __ldg(ee.xb + c);
+                b0.add(v, g1);
+            }
+            a0.add(v, g0);
+        } else if (steps < 4) {                   // a short slice: its 2-3 steps as one batch
             const int rem = steps;                // warp-uniform
             V v[3], g0[3], g1[3];
             int c[3];

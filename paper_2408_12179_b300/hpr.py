@@ -104,6 +104,7 @@ SIGNATURES = {
                                          ctypes.c_void_p, ctypes.c_void_p, _D, _I64]),
     "hpr_get_layout": (ctypes.c_int, [ctypes.c_void_p, _I64, _D, _I64]),
     "hpr_memory_probe": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, _D, _D]),
+    "hpr_fp64_probe": (ctypes.c_int, [ctypes.c_void_p, _D]),
     "hpr_bounds_violations": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
     "hpr_layout_plan": (ctypes.c_int, [ctypes.POINTER(hpr_csr), ctypes.c_int64, ctypes.c_double, _I64, _I64,
                                        _I64, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_uint8), _I32, _I32,
@@ -292,6 +293,14 @@ def bounds_violations() -> int:
     c = ctypes.c_int64()
     _check(load().hpr_bounds_violations(ctypes.byref(c)), None)
     return int(c.value)
+
+
+def fp64_probe(stream=None):
+    """FP64 warp instructions per second of the whole GPU, in 1e9/s (see hpr_fp64_probe in
+    include/hpr.h)."""
+    r = ctypes.c_double()
+    _check(load().hpr_fp64_probe(stream, ctypes.byref(r)), None)
+    return r.value
 
 
 def memory_probe(read_bytes=72_000_000, gather_len=1 << 18, stream=None):

@@ -124,7 +124,9 @@ def test_status_strings(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(sell_steps_a=-1), dict(sell_steps_t=5000), dict(unit_cost_t=-2.0),
-                                 dict(autotune=2), dict(halpern=3), dict(reflect=-1), dict(precision=2)])
+                                 dict(autotune=2), dict(halpern=3), dict(reflect=-1), dict(precision=2),
+                                 dict(gather_tiles=3), dict(gather_tiles=-1), dict(tile_len=1),
+                                 dict(tile_len=70000)])
 def test_invalid_options_rejected(lib, bad):
     lp = _tiny()
     with pytest.raises(hpr.HprError) as e:
