@@ -36,9 +36,16 @@ BATCH_METRIC = "HPR iterations/s summed over the LPs of the batch workload (LPs 
 # FP64; see profiles/), valid only for that workload and the kernel source they were
 # taken on.
 NCU_TRAFFIC = {
-    "source_sha1": "773e748f071a947ef233fe86cc11a676d2e263e8",
-    "k_phase_x": 87482368,
-    "k_phase_y": 72112128,
+    "source_sha1": "5d2582d12f53f06f041989718808621ee9706288",
+    "k_phase_x": 87558656,
+    "k_phase_y": 72121600,
+}
+# FP64 warp instructions per launch (ncu smsp__inst_executed_pipe_fp64.sum) of the phase
+# kernels on the same workload and kernel source (profiles/k_sell_traffic_medium_lp.md)
+NCU_FP64 = {
+    "source_sha1": "5d2582d12f53f06f041989718808621ee9706288",
+    "k_phase_x": 290668,
+    "k_phase_y": 203226,
 }
 
 
@@ -165,9 +172,10 @@ VARIANTS = {
 def fp64_per_launch(hpr, lp, layout, phase):
     """FP64 warp instructions of one normal-iteration launch of a phase in the FP64 form,
     counted from its sliced-ELL layout (hpr_layout_plan, the layout hpr_create builds): one
-    DFMA per 32 stored entries, one DADD merging the two FMA chains of a slice of 4 or more
-    steps, log2(lanes per row) DADDs of the row's lane butterfly per slice, and the epilogue's
-    five FP64 instructions (DADD, DFMA, DFMA, DMUL, DFMA) per work unit (each unit applies its
+    DFMA per 32 stored entries (three for a slice of 2 or 3 steps, whose batch issues its
+    FMAs predicated), one DADD merging the two FMA chains of a slice of 4 or more steps,
+    log2(lanes per row) DADDs of the row's lane butterfly per slice, and the epilogue's five
+    FP64 instructions (DADD, DFMA, DFMA, DMUL, DFMA) per work unit (each unit applies its
     32-row buffer once)."""
     import numpy as np
 
@@ -176,8 +184,8 @@ def fp64_per_launch(hpr, lp, layout, phase):
     L = hpr.layout_plan(M, int(layout["sell_steps"][k]), float(layout["unit_cost"][k]))
     steps = np.diff(L["sptr"]) // 32
     units = len(L["wstart"]) - 1
-    return int(L["sptr"][-1] // 32 + np.count_nonzero(steps >= 4) + int(L["slg"].astype(np.int64).sum())
-               + 5 * units)
+    return int(L["sptr"][-1] // 32 + np.count_nonzero(steps == 2) + np.count_nonzero(steps >= 4)
+               + int(L["slg"].astype(np.int64).sum()) + 5 * units)
 
 
 def bucket_of(lp):
@@ -502,11 +510,15 @@ def run_ours(args):
     fp64 = None
     if args.precision == 0 and not args.autotune:
         f_peak = hpr.fp64_probe(stream.cuda_stream)
-        f_inst = fp64_per_launch(hpr, lp, layout, "x" if dom == "k_phase_x" else "y")
+        f_model = fp64_per_launch(hpr, lp, layout, "x" if dom == "k_phase_x" else "y")
+        f_inst, f_src = f_model, "counted from the layout"
+        if traffic is not None and NCU_FP64["source_sha1"] == NCU_TRAFFIC["source_sha1"]:
+            f_inst, f_src = NCU_FP64[dom], "ncu smsp__inst_executed_pipe_fp64.sum"
         f_ach = f_inst / (dom_ms * 1e-3) / 1e9
         f_ach_graph = f_inst / (dom_in_graph_ms * 1e-3) / 1e9
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         fp64 = {"bound": "alu", "unit": "G FP64 warp instructions/s", "instructions_per_launch": f_inst,
+                "instructions_source": f_src, "instructions_model": f_model,
                 "achieved": f_ach, "peak": f_peak, "frac": f_ach / f_peak,
                 "in_graph_frac": f_ach_graph / f_peak,
                 "peak_source": "hpr_fp64_probe (independent DFMA chains, this run)",
