@@ -167,8 +167,9 @@ typedef struct {
                                  0 (default): the sliced-ELL kernel, which gathers y from L2;
                                  1: gather-tiled when the x phase moves at least 40 MB (12 nnz +
                                  60 n + 8 m bytes) and y takes at most one block per 4 SMs;
-                                 2: gather-tiled whenever y takes at most one block per SM
-                                 (HPR_ERR_ARG at hpr_create otherwise).  Gather-tiled: y is
+                                 2: gather-tiled whenever y takes at most one block per SM and
+                                 the layout's offsets fit in 32 bits (HPR_ERR_ARG at hpr_create
+                                 otherwise).  Gather-tiled: y is
                                  cut into blocks of consecutive entries that fit one CTA's
                                  shared memory, each CTA (one per SM) stages one block and
                                  streams the entries of A^T whose columns lie in it, the

@@ -443,10 +443,11 @@ SellHost build_sell(const std::vector<int> &rp, const std::vector<int> &ci, int 
 // in renumbered order) take the sliced-ELL layout of build_sell with column offsets within
 // the block.  Slot q of P holds a sub-row's sum; row r owns slots slot_ptr[r] ..
 // slot_ptr[r+1]-1, in block order.  A work unit is a run of consecutive slices of one block.
-// Rows are in the order perm, columns renamed by icol
-// (the renumbering of the sliced-ELL layout).  Returns false (layout not built) when the
-// blocks would outnumber the grid's CTAs or k_tile_epi's counter reset.
-// work units of the tiled layout: runs of slices of one block, each slice costing its steps
+// Rows are in the order perm, columns renamed by icol (the renumbering of the sliced-ELL
+// layout).  Returns false (layout not built) when the blocks would outnumber the grid's CTAs
+// or k_tile_epi's counter reset, or when the layout's offsets would not fit in 32 bits.
+//
+// Work units of the tiled layout: runs of slices of one block, each slice costing its steps
 // + 4; a block's units are sized so that each warp of its CTAs gets about TILE_UNITS_PER_WARP
 // of them (at least TILE_UNIT_MIN)
 constexpr int TILE_UNITS_PER_WARP = 4;
@@ -569,6 +570,16 @@ bool build_tiles(const std::vector<int> &rp, const std::vector<int> &ci, int row
                 for (int b = t; b < nblk; b += nthr) lay(b);
             });
         for (auto &th : pool) th.join();
+    }
+    // the concatenated offsets are 32-bit: a layout whose stored entries (padding included)
+    // or sub-rows reach 2^31 - 1 is not built
+    {
+        int64_t ents = 0, subs = 0;
+        for (int b = 0; b < nblk; ++b) {
+            ents += (int64_t)bh[(size_t)b].col.size();
+            subs += (int64_t)brow[(size_t)b].size();
+        }
+        if (ents >= (int64_t)INT32_MAX || subs >= (int64_t)INT32_MAX) return false;
     }
     // concatenation: slices, entries, sub-rows and units of block b follow those of b - 1
     h.ustart.assign(1, 0);
@@ -1361,7 +1372,8 @@ int upload_and_prepare(hpr_ctx *ctx, const hpr_csr *A1, const hpr_csr *A2, const
                           (!smallT && (m + len - 1) / len <= ctx->num_sms / 4);
         if (want) tiles = build_tiles(trp, tci, (int)n, pc, ipr, (int)m, len, ctx->num_sms, stepsT, costT, hX);
         if (!tiles && op.gather_tiles == 2)
-            return fail_arg(ctx, HPR_ERR_ARG, "gather_tiles = 2: y needs more blocks than the GPU has SMs");
+            return fail_arg(ctx, HPR_ERR_ARG, "gather_tiles = 2: y needs more blocks than the GPU has SMs, "
+                                              "or the layout's offsets exceed 32 bits");
     }
     std::vector<unsigned char> ineq((size_t)m);
     for (int64_t i = 0; i < m; ++i) ineq[(size_t)i] = pr[(size_t)i] >= m1 ? 1 : 0;
