@@ -399,6 +399,33 @@ int hpr_layout_plan(const hpr_csr *B, int64_t steps_max, double unit_cost, int64
                     int64_t *units, int32_t *row_order, int32_t *srow, int32_t *sptr, uint8_t *slg, int32_t *col,
                     int32_t *src, int32_t *wstart);
 
+/* Host only (no device work, no context; for tests): the gather-tiled layout that hpr_create
+ * builds for the x phase when hpr_options.gather_tiles asks for it (no counterpart in the
+ * paper), here for the rows of the CSR matrix B with B's own column numbering and rows in
+ * order of decreasing length (stable, row_order).  The gathered vector (B's columns) is cut
+ * into nblk blocks of consecutive entries, at most tile_len (taken even) each and starting
+ * at even indices, balanced by stored entries (bstart, nblk + 1).  Each block gets CTAs of
+ * a grid of `grid` in proportion to its entries, at least one each (cta_blk, grid).  The
+ * entries of each block form a sub-matrix whose rows (sub-rows: the rows with an entry in
+ * the block, in row_order) take hpr_layout_plan's sliced-ELL layout (40, 64) with column
+ * offsets within the block; slices and sub-rows of block b follow those of block b - 1.
+ * smeta (4 per slice): first sub-row, first stored entry, steps (32 entries each), log2
+ * lanes per sub-row | sub-rows << 8.  Work units are runs of slices of one block (wstart,
+ * units + 1); block b owns units ustart[b] .. ustart[b+1]-1.  Sub-row t's sum goes to slot
+ * oslot[t]; row r (in row_order position r) owns slots slot_ptr[r] .. slot_ptr[r+1]-1, one per
+ * block holding an entry of it, in block order.  col: the column offset within the block of
+ * each stored entry (padding: 0); src: its position in B's CSR arrays (padding: -1).
+ *   tile_len in [2, 65536], grid in [1, 65536].  Sizes go to sizes[0..5] = nblk, slices,
+ *   stored entries, sub-rows (slots), units, grid (sizes may be NULL).  Each array may be
+ *   NULL, else it must hold: row_order rows, bstart and ustart nblk + 1, cta_blk grid,
+ *   wstart units + 1, smeta 4 x slices, oslot sub-rows, slot_ptr rows + 1, col and src
+ *   entries.  Returns HPR_OK, or HPR_ERR_ARG (bad matrix or parameters, or a layout that
+ *   would need more blocks than min(grid, 256) or offsets beyond 32 bits; detail in
+ *   hpr_last_error(NULL)). */
+int hpr_tile_plan(const hpr_csr *B, int64_t tile_len, int64_t grid, int64_t *sizes, int32_t *row_order,
+                  int32_t *bstart, int32_t *ustart, int32_t *cta_blk, int32_t *wstart, int32_t *smeta,
+                  int32_t *oslot, int32_t *slot_ptr, uint16_t *col, int32_t *src);
+
 /* ---- Batched solve (no counterpart in the paper: many independent LPs in lock step).
  * A batch takes `count` contexts made by hpr_create (their LPs may differ in size and
  * structure) and solves them together: each check period's normal iterations of all

@@ -1018,6 +1018,67 @@ int hpr_layout_plan(const hpr_csr *B, int64_t steps_max, double unit_cost, int64
     return HPR_OK;
 }
 
+int hpr_tile_plan(const hpr_csr *B, int64_t tile_len, int64_t grid, int64_t *sizes, int32_t *row_order,
+                  int32_t *bstart, int32_t *ustart, int32_t *cta_blk, int32_t *wstart, int32_t *smeta,
+                  int32_t *oslot, int32_t *slot_ptr, uint16_t *col, int32_t *src)
+{
+    if (!B || B->rows < 1 || B->cols < 1 || B->nnz < 0 || B->rows >= (int64_t)INT32_MAX ||
+        B->cols >= (int64_t)INT32_MAX || B->nnz >= (int64_t)INT32_MAX || !B->row_ptr ||
+        (B->nnz > 0 && !B->col_idx) || tile_len < 2 || tile_len > 65536 || grid < 1 || grid > 65536) {
+        g_static_err = "hpr_tile_plan: bad matrix or parameters";
+        return HPR_ERR_ARG;
+    }
+    const int rows = (int)B->rows;
+    if (B->row_ptr[0] != 0 || B->row_ptr[rows] != B->nnz) {
+        g_static_err = "hpr_tile_plan: row_ptr[0] != 0 or row_ptr[rows] != nnz";
+        return HPR_ERR_ARG;
+    }
+    std::vector<int> rp((size_t)rows + 1), ci((size_t)std::max<int64_t>(B->nnz, 1), 0), icol((size_t)B->cols);
+    for (int i = 0; i <= rows; ++i) {
+        rp[(size_t)i] = (int)B->row_ptr[i];
+        if (i > 0 && rp[(size_t)i] < rp[(size_t)i - 1]) {
+            g_static_err = "hpr_tile_plan: row_ptr decreases";
+            return HPR_ERR_ARG;
+        }
+    }
+    for (int64_t p = 0; p < B->nnz; ++p) {
+        if (B->col_idx[p] < 0 || B->col_idx[p] >= B->cols) {
+            g_static_err = "hpr_tile_plan: column index out of range";
+            return HPR_ERR_ARG;
+        }
+        ci[(size_t)p] = B->col_idx[p];
+    }
+    for (int64_t j = 0; j < B->cols; ++j) icol[(size_t)j] = (int)j;
+    const std::vector<int> perm = order_by_length(rp, rows);
+    TileHost H;
+    if (!build_tiles(rp, ci, rows, perm, icol, (int)B->cols, (int)tile_len, (int)grid, SELL_STEPS, UNIT_COST, H)) {
+        g_static_err = "hpr_tile_plan: the blocks would outnumber the grid's CTAs (or 256), or the offsets exceed 32 bits";
+        return HPR_ERR_ARG;
+    }
+    if (sizes) {
+        sizes[0] = H.nblk;
+        sizes[1] = (int64_t)H.smeta.size();
+        sizes[2] = (int64_t)H.col.size();
+        sizes[3] = (int64_t)H.oslot.size();
+        sizes[4] = (int64_t)H.wstart.size() - 1;
+        sizes[5] = (int64_t)H.cta_blk.size();
+    }
+    auto put = [](int32_t *dst, const std::vector<int> &v) {
+        if (dst && !v.empty()) memcpy(dst, v.data(), sizeof(int32_t) * v.size());
+    };
+    put(row_order, perm);
+    put(bstart, H.bstart);
+    put(ustart, H.ustart);
+    put(cta_blk, H.cta_blk);
+    put(wstart, H.wstart);
+    put(oslot, H.oslot);
+    put(slot_ptr, H.slot_ptr);
+    put(src, H.src);
+    if (smeta && !H.smeta.empty()) memcpy(smeta, H.smeta.data(), sizeof(int4) * H.smeta.size());
+    if (col && !H.col.empty()) memcpy(col, H.col.data(), sizeof(uint16_t) * H.col.size());
+    return HPR_OK;
+}
+
 int hpr_get_checks(const hpr_ctx *ctx, hpr_check_record *out, int64_t cap, int64_t *count)
 {
     if (!ctx) return HPR_ERR_ARG;

@@ -109,6 +109,8 @@ SIGNATURES = {
     "hpr_layout_plan": (ctypes.c_int, [ctypes.POINTER(hpr_csr), ctypes.c_int64, ctypes.c_double, _I64, _I64,
                                        _I64, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_uint8), _I32, _I32,
                                        _I32]),
+    "hpr_tile_plan": (ctypes.c_int, [ctypes.POINTER(hpr_csr), ctypes.c_int64, ctypes.c_int64, _I64, _I32, _I32,
+                                     _I32, _I32, _I32, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_uint16), _I32]),
     "hpr_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "hpr_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
@@ -201,6 +203,30 @@ def layout_plan(M, steps_max=40, unit_cost=64.0):
                                _ptr(out["row_order"], _I32), _ptr(out["srow"], _I32), _ptr(out["sptr"], _I32),
                                _ptr(out["slg"], ctypes.POINTER(ctypes.c_uint8)), _ptr(out["col"], _I32),
                                _ptr(out["src"], _I32), _ptr(out["wstart"], _I32)))
+    del keep
+    return out
+
+
+def tile_plan(M, tile_len, grid=148):
+    """The gather-tiled layout of the x phase for the rows of the SciPy CSR matrix M (host
+    only, no GPU; see hpr_tile_plan in include/hpr.h): dict of numpy arrays row_order, bstart,
+    ustart, cta_blk, wstart, smeta (slices x 4), oslot, slot_ptr, col (uint16), src."""
+    lib = load()
+    B, keep = _block(M, M.shape[1])
+    sz = np.zeros(6, np.int64)
+    _check(lib.hpr_tile_plan(ctypes.byref(B), int(tile_len), int(grid), _ptr(sz, _I64), None, None, None, None,
+                             None, None, None, None, None, None))
+    nblk, ns, ne, nsub, nu, g = (int(v) for v in sz)
+    out = dict(row_order=np.zeros(M.shape[0], np.int32), bstart=np.zeros(nblk + 1, np.int32),
+               ustart=np.zeros(nblk + 1, np.int32), cta_blk=np.zeros(g, np.int32),
+               wstart=np.zeros(nu + 1, np.int32), smeta=np.zeros((ns, 4), np.int32),
+               oslot=np.zeros(nsub, np.int32), slot_ptr=np.zeros(M.shape[0] + 1, np.int32),
+               col=np.zeros(ne, np.uint16), src=np.zeros(ne, np.int32))
+    _check(lib.hpr_tile_plan(ctypes.byref(B), int(tile_len), int(grid), None, _ptr(out["row_order"], _I32),
+                             _ptr(out["bstart"], _I32), _ptr(out["ustart"], _I32), _ptr(out["cta_blk"], _I32),
+                             _ptr(out["wstart"], _I32), _ptr(out["smeta"], _I32), _ptr(out["oslot"], _I32),
+                             _ptr(out["slot_ptr"], _I32), _ptr(out["col"], ctypes.POINTER(ctypes.c_uint16)),
+                             _ptr(out["src"], _I32)))
     del keep
     return out
 
