@@ -85,6 +85,9 @@ int solve_begin(hpr_ctx *ctx, double tol)
     }
     st = ensure_ctl(ctx, (int)std::min<int64_t>(o.check_every, o.max_iter));
     if (st) return st;
+    // the gather-tiled x phase's work counters start at zero (k_tile_epi resets them after
+    // each k_tile_part; a launch that failed in between would leave them set)
+    if (ctx->TX.nblk) CK(cudaMemsetAsync(ctx->TX.ctr, 0, sizeof(unsigned) * (size_t)ctx->TX.nblk, s));
 
     CK(cudaStreamSynchronize(s));
     SolveState &S = ctx->ss;
@@ -1126,6 +1129,7 @@ int hpr_time_iteration(hpr_ctx *ctx, int64_t reps, double *ms_x, double *ms_y, d
     h->h[0] = 1.0 / 1002.0;
     h->h[1] = 1001.0 / 1002.0;
     CK(cudaMemcpyAsync(ctx->ctl, h, sizeof(DevCtl), cudaMemcpyHostToDevice, s));
+    if (ctx->TX.nblk) CK(cudaMemsetAsync(ctx->TX.ctr, 0, sizeof(unsigned) * (size_t)ctx->TX.nblk, s));
     // reps back-to-back iterations (phase X, phase Y) with events between the phases and no
     // host synchronisation in between, so the launch queue stays ahead of the GPU; the first
     // two iterations are left out of the averages (the queue fills during them)
