@@ -3,8 +3,9 @@
 //
 // The sliced-ELL phase kernel (k_sell) gathers one random 8-byte entry of y from L2 per
 // stored entry of A^T, and B300 serves such gathers at ~0.95 per clock per SM: on the
-// medium planted LP (5.25 M gathers a phase) that rate, not HBM, sets the x phase's time.
-// Shared memory serves random 8-byte loads ~5x faster.  So y is cut into blocks of
+// medium planted LP (5.25 M gathers a phase) that rate is one of the x phase's three
+// ceilings, beside HBM and FP64 issue.  Shared memory serves random 8-byte loads ~5x
+// faster.  So y is cut into blocks of
 // consecutive entries that fit one CTA's shared memory, and A^T into the sub-matrices
 // T_b holding the entries whose column (a row of A) lies in block b:
 //
@@ -19,6 +20,12 @@
 // Every sub-row's sum is a fixed function of the layout and the slots are added in a fixed
 // order, so results are bitwise reproducible whichever CTA takes which unit.  The row sums
 // are those of the sliced-ELL kernel in another order of addition (FP64 throughout).
+//
+// Measured on the medium planted LP, the pair is slower than k_sell (41 against 35 us):
+// the split adds FP64 instructions (a row becomes up to one sub-row per block, each with
+// its own chain merge; one add per slot; the epilogue in a kernel of its own), and FP64
+// issue is B300's scarcest resource.  The layout is therefore opt-in
+// (hpr_options.gather_tiles).
 #pragma once
 
 #include "hpr_device.cuh"
